@@ -1,0 +1,323 @@
+"""FP64 CPU oracle for the cone-beam CT hot path (TIGRE v3, Biguri et al.).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library: the projectors live in
+``oracle.c`` (plain C, FP64) and the iterative solvers below are written out in
+numpy FP64 in the order the textbook algorithms state them.
+
+Parity pins live in ``tests/test_oracle_*.py``.  Functions and the passage they
+follow:
+
+* ``frames`` -- geometry of Sec. 2.4 and the Appendix B parameter table.
+* ``forward(method="interp")`` -- Eq. 1, ray-driven trilinear sampling reading.
+* ``forward(method="siddon")`` -- Eq. 1 with exact intersection lengths.
+* ``backproject(method="matched")`` -- A^T of the interpolated projector
+  (Eq. 4 uses A^T), scatter form.
+* ``backproject(method="siddon")`` -- A^T of the Siddon projector.
+* ``fdk_filter``, ``backproject(method="fdk")``, ``fdk`` -- FDK (Sec. 2.1,
+  direct methods).
+* ``sirt``, ``ossart`` -- Kaczmarz-type methods (Sec. 2.1) with the ordered
+  subsets update (Sec. 2.2.2, Eq. 6).
+* ``cgls`` -- CGLS (Sec. 2.1, Krylov methods; Hestenes and Stiefel).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-D_DEFAULT_SOURCE",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Geo(ctypes.Structure):
+    _fields_ = [
+        ("nVoxel", ctypes.c_int32 * 3),
+        ("dVoxel", ctypes.c_double * 3),
+        ("nDetector", ctypes.c_int32 * 2),
+        ("dDetector", ctypes.c_double * 2),
+        ("accuracy", ctypes.c_double),
+        ("nAngles", ctypes.c_int32),
+        ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("DSO", ctypes.POINTER(ctypes.c_double)),
+        ("DSD", ctypes.POINTER(ctypes.c_double)),
+        ("offOrigin", ctypes.POINTER(ctypes.c_double)),
+        ("offDetector", ctypes.POINTER(ctypes.c_double)),
+        ("rotDetector", ctypes.POINTER(ctypes.c_double)),
+        ("COR", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int32)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            G = ctypes.POINTER(_Geo)
+            for name, args in {
+                "or_frames": [G, _DP],
+                "or_forward_interp": [G, _DP, _DP],
+                "or_forward_interp_rays": [G, _DP, ctypes.c_long, _IP, _DP],
+                "or_forward_siddon": [G, _DP, _DP],
+                "or_forward_siddon_rays": [G, _DP, ctypes.c_long, _IP, _DP],
+                "or_backproject_matched": [G, _DP, _DP],
+                "or_backproject_matched_voxels": [G, _DP, ctypes.c_long, _IP, _DP],
+                "or_backproject_siddon": [G, _DP, _DP],
+                "or_fdk_filter": [G, _DP, _DP],
+                "or_backproject_fdk": [G, _DP, _DP],
+                "or_backproject_fdk_voxels": [G, _DP, ctypes.c_long, _IP, _DP],
+            }.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = None
+            lib.or_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle uses (OMP_NUM_THREADS, else all cores)."""
+    return int(_load().or_num_threads())
+
+
+class _GeoHolder:
+    """Keeps the FP64 per-angle arrays alive while C holds pointers to them."""
+
+    def __init__(self, geo):
+        n = int(geo.nAngles)
+        self.arrays = {
+            "angles": np.ascontiguousarray(np.asarray(geo.angles, np.float64).reshape(n, 3)),
+            "DSO": np.ascontiguousarray(np.asarray(geo.DSO, np.float64).reshape(n)),
+            "DSD": np.ascontiguousarray(np.asarray(geo.DSD, np.float64).reshape(n)),
+            "offOrigin": np.ascontiguousarray(np.asarray(geo.offOrigin, np.float64).reshape(n, 3)),
+            "offDetector": np.ascontiguousarray(np.asarray(geo.offDetector, np.float64).reshape(n, 2)),
+            "rotDetector": np.ascontiguousarray(np.asarray(geo.rotDetector, np.float64).reshape(n, 3)),
+            "COR": np.ascontiguousarray(np.asarray(geo.COR, np.float64).reshape(n)),
+        }
+        g = _Geo()
+        g.nVoxel[:] = [int(v) for v in geo.nVoxel]
+        g.dVoxel[:] = [float(v) for v in geo.dVoxel]
+        g.nDetector[:] = [int(v) for v in geo.nDetector]
+        g.dDetector[:] = [float(v) for v in geo.dDetector]
+        g.accuracy = float(geo.accuracy)
+        g.nAngles = n
+        for k, arr in self.arrays.items():
+            setattr(g, k, arr.ctypes.data_as(_DP))
+        self.g = g
+        self.nx, self.ny, self.nz = (int(v) for v in geo.nVoxel)
+        self.nu, self.nv = (int(v) for v in geo.nDetector)
+        self.n = n
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.g)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def frames(geo) -> dict:
+    """Per-angle source S, detector centre D, pixel axes eu, ev, normal n (mm,
+    volume-centred frame), each of shape [nAngles, 3]."""
+    h = _GeoHolder(geo)
+    out = np.zeros((h.n, 15))
+    _load().or_frames(h.ref, _dp(out))
+    return {"S": out[:, 0:3], "D": out[:, 3:6], "eu": out[:, 6:9], "ev": out[:, 9:12], "n": out[:, 12:15]}
+
+
+def pixel_centres(geo, a: int) -> np.ndarray:
+    """Centres [nv, nu, 3] of the detector pixels of projection ``a``."""
+    f = frames(geo)
+    nu, nv = (int(v) for v in geo.nDetector)
+    su = ((np.arange(nu) + 0.5) - 0.5 * nu) * geo.dDetector[0]
+    sv = ((np.arange(nv) + 0.5) - 0.5 * nv) * geo.dDetector[1]
+    return (f["D"][a][None, None, :] + su[None, :, None] * f["eu"][a][None, None, :]
+            + sv[:, None, None] * f["ev"][a][None, None, :])
+
+
+def forward(geo, vol, method: str = "interp") -> np.ndarray:
+    """A x for the whole geometry: vol [nz, ny, nx] -> proj [nAngles, nv, nu]."""
+    h = _GeoHolder(geo)
+    v = _f64(vol).reshape(h.nz, h.ny, h.nx)
+    out = np.zeros((h.n, h.nv, h.nu))
+    fn = {"interp": _load().or_forward_interp, "siddon": _load().or_forward_siddon}[method]
+    if h.n:
+        fn(h.ref, _dp(v), _dp(out))
+    return out
+
+
+def forward_rays(geo, vol, rays, method: str = "interp") -> np.ndarray:
+    """A x on selected rays only; ``rays`` is an int array [m, 3] of (angle, iv, iu)."""
+    h = _GeoHolder(geo)
+    v = _f64(vol).reshape(h.nz, h.ny, h.nx)
+    r = np.ascontiguousarray(np.asarray(rays, np.int32).reshape(-1, 3))
+    out = np.zeros(len(r))
+    fn = {"interp": _load().or_forward_interp_rays, "siddon": _load().or_forward_siddon_rays}[method]
+    fn(h.ref, _dp(v), len(r), r.ctypes.data_as(_IP), _dp(out))
+    return out
+
+
+def backproject(geo, proj, method: str = "matched") -> np.ndarray:
+    """proj [nAngles, nv, nu] -> vol [nz, ny, nx].
+
+    ``matched``: A^T of the interpolated projector; ``siddon``: A^T of the
+    Siddon projector; ``fdk``: the FDK distance-weighted backprojection (the
+    input is expected to be already filtered)."""
+    h = _GeoHolder(geo)
+    p = _f64(proj).reshape(h.n, h.nv, h.nu)
+    out = np.zeros((h.nz, h.ny, h.nx))
+    fn = {"matched": _load().or_backproject_matched, "siddon": _load().or_backproject_siddon,
+          "fdk": _load().or_backproject_fdk}[method]
+    if h.n:
+        fn(h.ref, _dp(p), _dp(out))
+    return out
+
+
+def backproject_voxels(geo, proj, voxels, method: str = "matched") -> np.ndarray:
+    """The backprojection at selected voxels only; ``voxels`` is [m, 3] of (ix, iy, iz)."""
+    h = _GeoHolder(geo)
+    p = _f64(proj).reshape(h.n, h.nv, h.nu)
+    vx = np.ascontiguousarray(np.asarray(voxels, np.int32).reshape(-1, 3))
+    out = np.zeros(len(vx))
+    fn = {"matched": _load().or_backproject_matched_voxels, "fdk": _load().or_backproject_fdk_voxels}[method]
+    fn(h.ref, _dp(p), len(vx), vx.ctypes.data_as(_IP), _dp(out))
+    return out
+
+
+def fdk_filter(geo, proj) -> np.ndarray:
+    """Cosine pre-weight and Ram-Lak row filter of every projection."""
+    h = _GeoHolder(geo)
+    p = _f64(proj).reshape(h.n, h.nv, h.nu)
+    out = np.zeros_like(p)
+    if h.n:
+        _load().or_fdk_filter(h.ref, _dp(p), _dp(out))
+    return out
+
+
+def fdk(geo, proj) -> np.ndarray:
+    """FDK reconstruction: filter, then distance-weighted backprojection."""
+    return backproject(geo, fdk_filter(geo, proj), "fdk")
+
+
+# ---------------------------------------------------------------------------
+# Iterative solvers (numpy FP64 over the C projectors).
+# ---------------------------------------------------------------------------
+
+def _safe_inv(a: np.ndarray) -> np.ndarray:
+    out = np.zeros_like(a)
+    nz = a != 0
+    out[nz] = 1.0 / a[nz]
+    return out
+
+
+def sirt_weights(geo):
+    """W = 1/(A 1) per ray and V = 1/(A^T 1) per voxel, 0 where the sum is 0."""
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    nu, nv = (int(v) for v in geo.nDetector)
+    W = _safe_inv(forward(geo, np.ones((nz, ny, nx))))
+    V = _safe_inv(backproject(geo, np.ones((geo.nAngles, nv, nu)), "matched"))
+    return W, V
+
+
+def sirt(geo, b, niter: int, lam: float = 1.0, nonneg: bool = True, x0=None):
+    """SIRT: x <- P(x + lam * V A^T W (b - A x)), P = clamp at 0 when
+    ``nonneg`` (ART with non-negativity, Sec. 2.1).  Returns (x, residual
+    norms ||A x_k - b|| after each iteration)."""
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    b = _f64(b)
+    x = np.zeros((nz, ny, nx)) if x0 is None else _f64(x0).copy()
+    W, V = sirt_weights(geo)
+    hist = []
+    for _ in range(niter):
+        r = W * (b - forward(geo, x))
+        x = x + lam * V * backproject(geo, r, "matched")
+        if nonneg:
+            x = np.maximum(x, 0.0)
+        hist.append(float(np.linalg.norm(forward(geo, x) - b)))
+    return x, np.array(hist)
+
+
+def subsets(n_angles: int, blocksize: int):
+    """Contiguous angle blocks of ``blocksize`` in acquisition order; the last
+    block holds the remainder."""
+    return [np.arange(s, min(s + blocksize, n_angles)) for s in range(0, n_angles, blocksize)]
+
+
+def ossart(geo, b, niter: int, blocksize: int, lam: float = 1.0, nonneg: bool = True, x0=None):
+    """OS-SART: for each block s in order, x <- P(x + lam V_s A_s^T W_s (b_s
+    - A_s x)) (Sec. 2.2.2, Eq. 6 with the SART row/column weights).  One
+    iteration visits every block once.  Returns (x, residual history)."""
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    b = _f64(b)
+    x = np.zeros((nz, ny, nx)) if x0 is None else _f64(x0).copy()
+    blocks = subsets(geo.nAngles, blocksize)
+    sub = [geo.subset(idx) for idx in blocks]
+    weights = [sirt_weights(g) for g in sub]
+    hist = []
+    for _ in range(niter):
+        for idx, g, (W, V) in zip(blocks, sub, weights):
+            r = W * (b[idx] - forward(g, x))
+            x = x + lam * V * backproject(g, r, "matched")
+            if nonneg:
+                x = np.maximum(x, 0.0)
+        hist.append(float(np.linalg.norm(forward(geo, x) - b)))
+    return x, np.array(hist)
+
+
+def cgls(geo, b, niter: int, x0=None):
+    """CGLS on min ||A x - b|| (Hestenes-Stiefel, applied to the normal
+    equations without forming them):
+        r = b - A x, s = A^T r, p = s, gamma = ||s||^2
+        repeat: q = A p; alpha = gamma / ||q||^2; x += alpha p; r -= alpha q
+                s = A^T r; gamma' = ||s||^2; p = s + (gamma'/gamma) p
+    Returns (x, ||r_k|| after each iteration)."""
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    b = _f64(b)
+    x = np.zeros((nz, ny, nx)) if x0 is None else _f64(x0).copy()
+    r = b - forward(geo, x)
+    s = backproject(geo, r, "matched")
+    p = s.copy()
+    gamma = float(np.sum(s * s))
+    hist = []
+    for _ in range(niter):
+        q = forward(geo, p)
+        qq = float(np.sum(q * q))
+        if qq == 0.0 or gamma == 0.0:
+            hist.append(float(np.linalg.norm(r)))
+            continue
+        alpha = gamma / qq
+        x = x + alpha * p
+        r = r - alpha * q
+        s = backproject(geo, r, "matched")
+        gamma_new = float(np.sum(s * s))
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+        hist.append(float(np.linalg.norm(r)))
+    return x, np.array(hist)

@@ -1,0 +1,121 @@
+"""Pins of the oracle's iterative solvers (SIRT / OS-SART, Sec. 2.1 and
+Sec. 2.2.2 Eq. 6; CGLS, Sec. 2.1 Krylov methods) on a tiny problem whose
+system matrix is materialised column by column, so that the solvers can be
+compared with dense linear algebra."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_10129_gb300 import inputs
+
+
+def tiny_geo(n_angles=3):
+    return inputs.circular_geometry((4, 4, 4), (1.0,) * 3, (8, 8), (0.9, 0.9), n_angles, 30.0, 50.0)
+
+
+def dense_A(g):
+    nvox = int(np.prod(g.vol_shape))
+    cols = []
+    for j in range(nvox):
+        e = np.zeros(nvox)
+        e[j] = 1.0
+        cols.append(oracle.forward(g, e.reshape(g.vol_shape), "interp").reshape(-1))
+    return np.stack(cols, axis=1)
+
+
+@pytest.fixture(scope="module")
+def problem():
+    g = tiny_geo()
+    A = dense_A(g)
+    rng = np.random.default_rng(0)
+    xt = rng.random(A.shape[1])
+    b = A @ xt + 0.01 * rng.standard_normal(A.shape[0])
+    return g, A, xt, b
+
+
+def test_dense_matrix_matches_backprojection(problem):
+    g, A, _, _ = problem
+    y = np.random.default_rng(1).random(A.shape[0])
+    np.testing.assert_allclose(oracle.backproject(g, y.reshape(g.proj_shape), "matched").reshape(-1),
+                               A.T @ y, rtol=1e-12, atol=1e-13)
+
+
+def test_cgls_reaches_least_squares_solution(problem):
+    g, A, _, b = problem
+    x, hist = oracle.cgls(g, b.reshape(g.proj_shape), 300)
+    ref = np.linalg.pinv(A) @ b   # minimum-norm least-squares solution
+    assert np.linalg.norm(x.reshape(-1) - ref) / np.linalg.norm(ref) < 1e-6
+    assert hist[-1] == pytest.approx(np.linalg.norm(A @ ref - b), rel=1e-8)
+
+
+def test_cgls_residual_is_monotone(problem):
+    g, _, _, b = problem
+    _, hist = oracle.cgls(g, b.reshape(g.proj_shape), 40)
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+
+
+def test_cgls_exact_data_and_warm_start(problem):
+    """Started at the exact solution of consistent data, CGLS does not move."""
+    g, A, xt, _ = problem
+    b = A @ xt
+    x, hist = oracle.cgls(g, b.reshape(g.proj_shape), 5, x0=xt.reshape(g.vol_shape))
+    np.testing.assert_allclose(x.reshape(-1), xt, rtol=0, atol=1e-12)
+    assert hist.max() < 1e-10
+
+
+def dense_sirt(A, b, niter, lam=1.0, nonneg=True, x0=None):
+    rs, cs = A.sum(1), A.sum(0)
+    W = np.where(rs != 0, 1.0 / np.where(rs != 0, rs, 1), 0.0)
+    V = np.where(cs != 0, 1.0 / np.where(cs != 0, cs, 1), 0.0)
+    x = np.zeros(A.shape[1]) if x0 is None else x0.copy()
+    for _ in range(niter):
+        x = x + lam * V * (A.T @ (W * (b - A @ x)))
+        if nonneg:
+            x = np.maximum(x, 0)
+    return x
+
+
+def test_sirt_matches_dense_iteration(problem):
+    g, A, _, b = problem
+    x, _ = oracle.sirt(g, b.reshape(g.proj_shape), 7, lam=0.9)
+    np.testing.assert_allclose(x.reshape(-1), dense_sirt(A, b, 7, lam=0.9), rtol=1e-10, atol=1e-12)
+
+
+def test_sirt_consistent_data_residual_decreases(problem):
+    g, A, xt, _ = problem
+    b = A @ xt
+    _, hist = oracle.sirt(g, b.reshape(g.proj_shape), 15, nonneg=False)
+    assert np.all(np.diff(hist) < 0)
+
+
+def test_sirt_single_voxel_single_ray():
+    """One voxel and one ray: W = V = 1/a so one step gives x = b / a."""
+    g = inputs.circular_geometry((1, 1, 1), (2.0,) * 3, (1, 1), (1.0, 1.0), 1, 50.0, 80.0)
+    a = float(oracle.forward(g, np.ones((1, 1, 1)), "interp")[0, 0, 0])
+    assert a > 0
+    x, _ = oracle.sirt(g, np.full((1, 1, 1), 3.0), 1)
+    assert x[0, 0, 0] == pytest.approx(3.0 / a, rel=1e-14)
+
+
+def test_ossart_one_block_is_sirt(problem):
+    g, _, _, b = problem
+    xs, _ = oracle.sirt(g, b.reshape(g.proj_shape), 3)
+    xo, _ = oracle.ossart(g, b.reshape(g.proj_shape), 3, blocksize=g.nAngles)
+    np.testing.assert_allclose(xo, xs, rtol=1e-13, atol=1e-15)
+
+
+def test_ossart_blocks_match_dense(problem):
+    g, A, _, b = problem
+    nrow = g.nDetector[0] * g.nDetector[1]
+    x = np.zeros(A.shape[1])
+    for _ in range(2):
+        for blk in oracle.subsets(g.nAngles, 2):
+            rows = np.concatenate([np.arange(a * nrow, (a + 1) * nrow) for a in blk])
+            x = dense_sirt(A[rows], b[rows], 1, x0=x)
+    xo, _ = oracle.ossart(g, b.reshape(g.proj_shape), 2, blocksize=2)
+    np.testing.assert_allclose(xo.reshape(-1), x, rtol=1e-10, atol=1e-12)
+
+
+def test_subsets_ragged_tail():
+    blocks = oracle.subsets(7, 3)
+    assert [list(b) for b in blocks] == [[0, 1, 2], [3, 4, 5], [6]]
