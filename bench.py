@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark: FP+BP voxel-samples/s on the 512^3 clinical cone-beam workload.
+
+Workload (synthetic, seeded): 512^3 FP32 volume at 0.5 mm holding a
+40-ellipsoid phantom, 720 angles over 2 pi, 768 x 1024 detector at 0.4 mm,
+DSO 1000 mm, DSD 1536 mm, measured data = Siddon projection of the phantom
+with Poisson noise at I0 = 1e5.
+
+One step = one pass over every operation of the hot path, each through the
+C ABI:
+  * tg_cgls, one iteration from x0 = 0 (two interpolated forward
+    projections, two matched backprojections, fused FP64 inner products and
+    vector updates),
+  * tg_forward with the Siddon projector,
+  * tg_fdk (cosine weight + Ram-Lak filter + FDK backprojection).
+Units: forward samples (trilinear samples taken, or Siddon voxel segments)
+plus backprojected voxel-angle pairs; value = units per step / step time.
+
+Timing: W untimed warm-up steps, then K steps between a barrier and
+torch.cuda.synchronize(), on CUDA events of the launching stream; max over
+ranks.  Inputs (0.5 GB volume, 2.3 GB projections) exceed the 129 MB L2, so
+no flush is needed between steps.  Multi-GPU runs are independent replicas
+(the operators shard, but one GPU holds the whole problem; no collective).
+``--impl reference`` times the CPU FP64 oracle on a bounded sample of the
+same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "FP+BP voxel-samples/s at 512^3 (% roofline); s to PSNR: learned vs CGLS"
+UNIT = "voxel-samples/s"
+WORKLOAD = "512^3 FP32 volume (0.5 mm), 720 angles over 2pi, 768x1024 detector (0.4 mm), 40-ellipsoid phantom"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+CASES = {
+    # name: (workload text, geometry factory, ellipsoids)
+    "clinical": (WORKLOAD, "config_clinical", 40),
+    # the same scan at half the resolution (profiling captures: inputs still
+    # exceed L2, one launch runs well under a second)
+    "medium": ("256^3 FP32 volume (1 mm), 360 angles over 2pi, 384x512 detector (0.8 mm), 20-ellipsoid phantom",
+               None, 20),
+}
+
+
+def make_inputs(case="clinical", seed=1):
+    from paper_2412_10129_gb300 import inputs
+    if case == "medium":
+        g = inputs.circular_geometry((256, 256, 256), (1.0,) * 3, (512, 384), (0.8, 0.8), 360, 1000.0, 1536.0)
+    else:
+        g = inputs.config_clinical()
+    x = inputs.ellipsoid_phantom(g, CASES[case][2], seed=seed)
+    return g, x
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU FP64 oracle on a bounded sample of the workload.
+# ---------------------------------------------------------------------------
+
+def oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=96, seed=0):
+    """Time the oracle: interpolated FP of every pixel of `n_fp_angles`
+    angles, matched BP (gather form) of `n_bp_voxels` voxels over all angles.
+    Returns (units, seconds, description)."""
+    import oracle
+    from paper_2412_10129_gb300 import tg
+    rng = np.random.default_rng(seed)
+    sub = g.subset(np.linspace(0, g.nAngles - 1, n_fp_angles).astype(int))
+    rays = np.stack(np.meshgrid(np.arange(sub.nAngles), np.arange(g.nDetector[1]), np.arange(g.nDetector[0]),
+                                indexing="ij"), -1).reshape(-1, 3)
+    vox = np.stack([rng.integers(0, n, n_bp_voxels) for n in g.nVoxel], 1)
+    t0 = time.perf_counter()
+    oracle.forward_rays(sub, x, rays, "interp")
+    t1 = time.perf_counter()
+    oracle.backproject_voxels(g, y, vox, "matched")
+    t2 = time.perf_counter()
+    fp_units = tg.count_samples(sub, "interp") if _gpu_ok() else _count_samples_host(sub)
+    units = fp_units + n_bp_voxels * g.nAngles
+    desc = (f"oracle interpolated FP of all {len(rays)} rays of {n_fp_angles} angle(s) ({fp_units} samples) + "
+            f"matched BP of {n_bp_voxels} random voxels x {g.nAngles} angles")
+    return units, t2 - t0, desc
+
+
+def _gpu_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
+
+
+def _count_samples_host(g):
+    """Samples of the interpolated projector, counted in FP64 on the host."""
+    import oracle
+    f = oracle.frames(g)
+    delta = g.accuracy * min(g.dVoxel)
+    h = 0.5 * np.asarray(g.nVoxel) * np.asarray(g.dVoxel)
+    total = 0
+    for a in range(g.nAngles):
+        P = oracle.pixel_centres(g, a).reshape(-1, 3)
+        S = f["S"][a]
+        d = P - S
+        L = np.linalg.norm(d, axis=1)
+        dh = d / L[:, None]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = (-h[None] - S[None]) / dh
+            tb = (h[None] - S[None]) / dh
+        lo = np.nanmax(np.minimum(ta, tb), axis=1).clip(min=0)
+        hi = np.minimum(np.nanmin(np.maximum(ta, tb), axis=1), L)
+        n = np.floor(hi / delta) - np.ceil(lo / delta) + 1
+        total += int(np.sum(np.where(hi >= lo, np.maximum(n, 0), 0)))
+    return total
+
+
+def cpu_cores():
+    try:
+        import oracle
+        return oracle.num_threads()
+    except Exception:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle, timed on the host cores.
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from paper_2412_10129_gb300 import inputs
+    g, x = make_inputs()
+    y = inputs.random_projections(g.subset(np.arange(g.nAngles)), seed=3)
+    for _ in range(args.warmup):
+        oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=32)
+    units = 0
+    secs = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        u, s, desc = oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=32)
+        units += u
+        secs += s
+    value = units / secs
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_per_step": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm.
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    from paper_2412_10129_gb300 import build, inputs, tg
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    build.build()
+    tg.load()
+    dev = torch.device("cuda", local)
+    g, x_np = make_inputs(args.case)
+    b_np = inputs.poisson_noise(_siddon_gpu(g, x_np, dev), 1e5, seed=2)
+    vol_elems = int(np.prod(g.vol_shape))
+    proj_elems = int(np.prod(g.proj_shape))
+    b = torch.from_numpy(b_np).to(dev)
+    x = torch.from_numpy(x_np).to(dev)
+    xw = torch.zeros(g.vol_shape, device=dev)
+    p_sid = torch.empty(g.proj_shape, device=dev)
+    v_fdk = torch.empty(g.vol_shape, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    s_interp = tg.count_samples(g, "interp")
+    s_siddon = tg.count_samples(g, "siddon")
+    bp_pairs = vol_elems * g.nAngles
+    units_cgls = 2 * s_interp + 2 * bp_pairs
+    units_step = units_cgls + s_siddon + bp_pairs
+
+    def step():
+        xw.zero_()
+        tg.cgls(g, b, 1, x0=xw)
+        tg.forward(g, x, "siddon", out=p_sid)
+        tg.fdk(g, b, out=v_fdk)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # per-kernel times (outside the headline): one launch each
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    p_tmp = torch.empty(g.proj_shape, device=dev)
+    v_tmp = torch.empty(g.vol_shape, device=dev)
+    t_fp = timed(lambda: tg.forward(g, x, "interp", out=p_tmp))
+    t_bp = timed(lambda: tg.backproject(g, b, "matched", out=v_tmp))
+    t_sid = timed(lambda: tg.forward(g, x, "siddon", out=p_tmp))
+    t_bpf = timed(lambda: tg.backproject(g, b, "fdk", out=v_tmp))
+    t_fdk = timed(lambda: tg.fdk(g, b, out=v_tmp))
+    del p_tmp, v_tmp
+    torch.cuda.empty_cache()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = tg.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    launches = tg.launch_count() - n0
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    secs = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
+    value = world * units_step * args.steps / secs
+
+    # end to end: the same step through the C ABI with pinned host buffers,
+    # host<->device copies inside the timed region
+    bh = torch.from_numpy(b_np).pin_memory()
+    xh = torch.from_numpy(x_np).pin_memory()
+    xwh = torch.zeros(g.vol_shape).pin_memory()
+    sidh = torch.empty(g.proj_shape).pin_memory()
+    fdkh = torch.empty(g.vol_shape).pin_memory()
+    h2d = 4 * (proj_elems + vol_elems) + 4 * vol_elems + 4 * proj_elems     # cgls (b, x0), siddon (x), fdk (b)
+    d2h = 4 * vol_elems + 4 * proj_elems + 4 * vol_elems                    # cgls x, siddon proj, fdk vol
+
+    def step_host():
+        xwh.zero_()
+        tg.cgls(g, bh, 1, x0=xwh)
+        tg.forward(g, xh, "siddon", out=sidh)
+        tg.fdk(g, bh, out=fdkh)
+
+    step_host()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    torch.cuda.synchronize(dev)
+    secs_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = world * units_step * args.steps / secs_e2e
+
+    pk, pk_kind = peaks()
+    # dominant kernel: the matched backprojector (largest share of a step)
+    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 4 * 32 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6   # lane-instructions/s at max clock
+    bp_ops = 32.0 * s_interp    # irreducible lane-ops of the transpose: 32 per sample
+    roof = {"bound": "alu", "achieved": bp_ops / t_bp / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
+            "frac": (bp_ops / t_bp) / alu_peak, "traffic": None,
+            "kernel": "k_bp_matched", "peak_source": f"152 SM x 4 SMSP x 32 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz "
+                                                      f"({pk_kind} max clock)",
+            "ops_per_unit": "32 FP32/INT32 lane-ops per interpolated sample (position, floor, weights, 8 products, 8 adds)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CASES[args.case][0], "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs (2.8 GB) exceed L2 (129 MB); no flush",
+                       "step": "tg_cgls 1 iteration + tg_forward(siddon) + tg_fdk",
+                       "units_per_step": units_step},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "roofline": roof,
+            "kernels_s": {"fp_interp": t_fp, "bp_matched": t_bp, "fp_siddon": t_sid, "bp_fdk": t_bpf,
+                          "fdk": t_fdk},
+            "rates": {"fp_interp_samples_per_s": s_interp / t_fp, "bp_matched_pairs_per_s": bp_pairs / t_bp,
+                      "fp_siddon_segments_per_s": s_siddon / t_sid, "bp_fdk_pairs_per_s": bp_pairs / t_bpf,
+                      "fp_plus_bp_matched": (s_interp + bp_pairs) / (t_fp + t_bp)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        y_np = b_np
+        units_c, secs_c, desc = oracle_sample(g, x_np, y_np, n_fp_angles=2, n_bp_voxels=128)
+        line["cpu_baseline"] = {"value": units_c / secs_c, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _siddon_gpu(g, x_np, dev):
+    import torch
+
+    from paper_2412_10129_gb300 import tg
+    return tg.forward(g, torch.from_numpy(x_np).to(dev), "siddon").cpu().numpy()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tg", choices=["tg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="clinical", choices=sorted(CASES),
+                    help="workload; 'medium' is the half-resolution scan used for profiler captures")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

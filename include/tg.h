@@ -1,0 +1,164 @@
+/*
+ * tg.h -- C ABI of libtg, GB300 (sm_103a) cone-beam CT projectors and
+ * iterative reconstruction.
+ *
+ * The operations follow TIGRE v3 (Biguri et al.):
+ *   - the linear model A x = b of Eq. 1 (Sec. 2.1), x the voxel volume and
+ *     b the projections, both in lexicographic order;
+ *   - the scan geometry of Sec. 2.4 and the geometry-parameter table of
+ *     Appendix B, every parameter except the sizes may vary per projection;
+ *   - FDK (Sec. 2.1, direct methods), SIRT and OS-SART (Sec. 2.1, Kaczmarz
+ *     type; Sec. 2.2.2, Eq. 6), CGLS (Sec. 2.1, Krylov methods).
+ *
+ * Layouts (all float32, C order, x fastest):
+ *   volume       vol [batch][nz][ny][nx]
+ *   projections  proj[batch][nAngles][nv][nu]      (u = detector column)
+ * Coordinates: millimetres in a frame whose origin is the volume centre
+ * placed at offOrigin; voxel i has its centre at ((i + 0.5) - n/2) * d.
+ * Per-angle frame: the source sits at DSO on +x of the rotating frame, the
+ * detector centre at DSO - DSD, pixel axes u = +y and v = +z; the detector
+ * is rotated in place by Rz(phi) Ry(theta) Rx(psi), shifted by offDetector
+ * along its own axes, source and detector are shifted by COR along y, the
+ * set-up is rotated by Rz(z1) Ry(y1) Rz(z2) (the ZYZ angles) and finally
+ * taken relative to offOrigin.  Pixel (iu, iv) has its centre at
+ * D + ((iu + 0.5) - nu/2) du eu + ((iv + 0.5) - nv/2) dv ev (the uv origin
+ * is the bottom-left detector corner).
+ *
+ * Buffers: every float buffer may be device memory (asynchronous on
+ * `stream`) or host memory (the call stages it through device memory,
+ * copies the result back and returns after the stream has finished).  The
+ * caller owns every buffer; the library never frees them.  Scratch memory
+ * is taken with cudaMallocAsync on `stream` and released before return.
+ *
+ * Errors: argument and geometry checks run on the host before any launch
+ * and return synchronously; kernel launch errors are read with
+ * cudaGetLastError and returned as TG_ERR_CUDA; allocation failure returns
+ * TG_ERR_OOM.  No call aborts the process.
+ */
+#ifndef TG_H
+#define TG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TG_OK = 0,
+    TG_ERR_ARG = 1,         /* null pointer, bad size, unknown method */
+    TG_ERR_GEOMETRY = 2,    /* non-positive sizes, DSD <= 0, DSO <= 0, ... */
+    TG_ERR_OOM = 3,         /* scratch allocation failed */
+    TG_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed */
+    TG_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    TG_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} tg_status;
+
+/* Forward projector discretisations (the paper names neither; see the
+ * readings in the design notes). */
+enum {
+    TG_INTERP = 0, /* b_i = delta * sum_k trilinear(x, S + k delta d_i): samples on a
+                      lattice fixed to the source, kept inside the closed volume box
+                      and on the source-pixel segment; delta = accuracy * min(dVoxel) */
+    TG_SIDDON = 1  /* b_i = sum_j x_j |segment_i & voxel_j| (exact lengths) */
+};
+
+/* Backprojectors. */
+enum {
+    TG_MATCHED = 0,    /* exact transpose of TG_INTERP (A^T of Eq. 4) */
+    TG_FDK_WEIGHT = 1  /* voxel-driven (DSO/L)^2 bilinear backprojection times pi/nAngles */
+};
+
+/* FDK filters. */
+enum { TG_RAMLAK = 0 };
+
+/* OS-SART block order. */
+enum { TG_ORDER_SEQUENTIAL = 0, TG_ORDER_RANDOM = 1 };
+
+/* Geometry (Appendix B parameter table).  Sizes are fixed across angles;
+ * each per-angle array has nAngles entries (or nAngles x 3 / x 2) and may be
+ * NULL, in which case the scalar default applies to every angle. */
+typedef struct {
+    int32_t nVoxel[3];        /* nx, ny, nz */
+    double dVoxel[3];         /* mm */
+    int32_t nDetector[2];     /* nu (columns), nv (rows) */
+    double dDetector[2];      /* mm */
+    double accuracy;          /* TG_INTERP sample step in units of min(dVoxel); <= 0 means 0.5 */
+    double DSO0, DSD0;        /* defaults for DSO, DSD (mm) */
+    const double *DSO;        /* [nAngles] or NULL */
+    const double *DSD;        /* [nAngles] or NULL */
+    const double *offOrigin;  /* [nAngles][3] or NULL (0) */
+    const double *offDetector;/* [nAngles][2] (u, v) or NULL (0) */
+    const double *rotDetector;/* [nAngles][3] (phi, theta, psi) rad or NULL (0) */
+    const double *COR;        /* [nAngles] or NULL (0) */
+} tg_geometry;
+
+/* Forward projection A x (Eq. 1).  angles: [nAngles][3] ZYZ (z1, y1, z2)
+ * in rad; a circular orbit passes (theta, 0, 0).  vol: [batch] volumes,
+ * proj: [batch] projection sets that share the geometry.  proj is
+ * overwritten.  nAngles == 0 or batch == 0 is a no-op. */
+tg_status tg_forward(const tg_geometry *geo, const double *angles, int nAngles, const float *vol,
+                     float *proj, int method, int batch, void *stream);
+
+/* Backprojection (A^T of Eq. 4 for TG_MATCHED, the FDK backprojection for
+ * TG_FDK_WEIGHT).  vol is overwritten. */
+tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngles,
+                         const float *proj, float *vol, int method, int batch, void *stream);
+
+/* FDK (Sec. 2.1, direct methods): cosine pre-weight |(P-S).n|/|P-S|, Ram-Lak
+ * row filter sampled at du*DSO/DSD (linear convolution, no wrap-around),
+ * TG_FDK_WEIGHT backprojection.  Assumes equally spaced angles over 2 pi.
+ * vol is overwritten; proj is not modified. */
+tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                 float *vol, int filter, void *stream);
+
+/* SIRT (Sec. 2.1): x <- P(x + lambda V A^T W (b - A x)), W = 1/(A 1),
+ * V = 1/(A^T 1) (0 where the sum is 0), P = clamp at 0 when nonneg != 0.
+ * A = TG_INTERP, A^T = TG_MATCHED.  vol holds x0 on entry and x on exit.
+ * resid_hist (nullable, host or device, niter doubles) receives
+ * ||A x_k - b|| after each iteration (one extra projection per iteration);
+ * a host resid_hist is valid after the call returns and the stream has
+ * synchronised. */
+tg_status tg_sirt(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                  float *vol, int niter, float lambda, int nonneg, double *resid_hist, void *stream);
+
+/* OS-SART (Sec. 2.2.2, Eq. 6 with SART weights): the SIRT update applied to
+ * blocks of `blocksize` consecutive angles (the last block holds the
+ * remainder) in acquisition order (TG_ORDER_SEQUENTIAL) or in an order
+ * drawn per iteration from `seed` (TG_ORDER_RANDOM).  One iteration visits
+ * every block once. */
+tg_status tg_ossart(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                    float *vol, int niter, int blocksize, int order, uint64_t seed, float lambda,
+                    int nonneg, double *resid_hist, void *stream);
+
+/* CGLS (Sec. 2.1, Hestenes-Stiefel on the normal equations, A = TG_INTERP,
+ * A^T = TG_MATCHED), inner products accumulated in FP64 on the device.  vol
+ * holds x0 on entry and x on exit.  resid_hist (nullable) receives the
+ * recurrence residual ||r_k|| after each iteration. */
+tg_status tg_cgls(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                  float *vol, int niter, double *resid_hist, void *stream);
+
+/* Bytes of device scratch a call would take (op: 0 forward, 1 backproject,
+ * 2 fdk, 3 sirt, 4 ossart, 5 cgls; blocksize only for ossart). */
+tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int batch, int blocksize,
+                            size_t *bytes);
+
+/* Units of work of one forward projection over all rays, written to *count
+ * on return (the call waits for `stream`): the number of samples the
+ * TG_INTERP projector keeps, or the number of voxel segments the TG_SIDDON
+ * projector visits.  Counts the work; computes no projection. */
+tg_status tg_count_samples(const tg_geometry *geo, const double *angles, int nAngles, int method,
+                           uint64_t *count, void *stream);
+
+/* Static text for a status code. */
+const char *tg_status_string(tg_status s);
+
+/* Number of kernel launches issued by this process so far (all calls). */
+uint64_t tg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TG_H */

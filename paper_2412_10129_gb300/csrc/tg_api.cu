@@ -1,0 +1,468 @@
+// tg_api.cu -- the C ABI of libtg (declared in include/tg.h): argument and
+// geometry validation, host-buffer staging, scratch management and the
+// solver loops (SIRT, OS-SART, CGLS) over the projector kernels.
+#include <math.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "tg_internal.cuh"
+
+namespace tg {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+tg_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TG_OK;
+    if (e == cudaErrorMemoryAllocation) return TG_ERR_OOM;
+    return TG_ERR_CUDA;
+}
+
+bool is_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// Per-call context: the stream, the scratch allocations (released with
+// cudaFreeAsync when the call ends) and the first error seen.
+struct Call {
+    cudaStream_t s;
+    std::vector<void *> bufs;
+    cudaError_t err = cudaSuccess;
+    bool sync_at_end = false;
+    bool done = false;
+    explicit Call(void *stream) : s((cudaStream_t)stream) {}
+    ~Call() { finish(); }
+    // Release the scratch (stream ordered) and, when results were staged
+    // into host memory, wait for the stream; returns the call's status.
+    tg_status finish() {
+        if (!done) {
+            done = true;
+            for (void *p : bufs) cudaFreeAsync(p, s);
+            bufs.clear();
+            if (sync_at_end) ok(cudaStreamSynchronize(s));
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) ok(e);
+        }
+        return status();
+    }
+    template <class T>
+    T *alloc(size_t count) {
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T) + 16, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (err == cudaSuccess) err = cudaErrorMemoryAllocation;
+            return nullptr;
+        }
+        bufs.push_back(p);
+        return (T *)p;
+    }
+    bool ok(cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        return err == cudaSuccess;
+    }
+    bool ok() const { return err == cudaSuccess; }
+    tg_status status() const { return from_cuda(err); }
+};
+
+// A caller buffer as seen by the kernels: the pointer itself when it is
+// device memory, else a device copy staged on the call's stream.
+template <class T>
+struct View {
+    T *user = nullptr;
+    T *dev = nullptr;
+    size_t count = 0;
+    bool staged = false;
+};
+
+template <class T>
+View<T> stage_in(Call &c, T *user, size_t count, bool copy_in) {
+    View<T> v;
+    v.user = user;
+    v.count = count;
+    if (!user || count == 0) {
+        v.dev = user;
+        return v;
+    }
+    if (!is_host(user)) {
+        v.dev = user;
+        return v;
+    }
+    v.staged = true;
+    c.sync_at_end = true;
+    v.dev = c.alloc<T>(count);
+    if (v.dev && copy_in)
+        c.ok(cudaMemcpyAsync((void *)v.dev, (const void *)user, count * sizeof(T), cudaMemcpyHostToDevice, c.s));
+    return v;
+}
+
+template <class T>
+void stage_out(Call &c, View<T> &v) {
+    if (v.staged && v.dev && c.ok())
+        c.ok(cudaMemcpyAsync((void *)v.user, v.dev, v.count * sizeof(T), cudaMemcpyDeviceToHost, c.s));
+}
+
+Angle *upload_angles(Call &c, const tg_geometry *geo, const double *angles, int nA) {
+    std::vector<Angle> h((size_t)(nA > 0 ? nA : 1));
+    build_angles(geo, angles, nA, h.data());
+    Angle *d = c.alloc<Angle>(h.size());
+    if (d) c.ok(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(Angle), cudaMemcpyHostToDevice, c.s));
+    return d;
+}
+
+size_t vol_count(const tg_geometry *g) { return (size_t)g->nVoxel[0] * g->nVoxel[1] * g->nVoxel[2]; }
+size_t proj_count(const tg_geometry *g, int nA) { return (size_t)nA * g->nDetector[0] * g->nDetector[1]; }
+
+// Launch description of a call: sizes, steps and the matched backprojector's
+// fixed-point weight bound.
+Grid call_grid(const tg_geometry *geo, const double *angles, int nA) {
+    Grid g = make_grid(geo, nA);
+    set_weight_bound(geo, angles, nA, g);
+    return g;
+}
+
+tg_status check_common(const tg_geometry *geo, const double *angles, int nA) {
+    if (!geo) return TG_ERR_ARG;
+    return validate_geometry(geo, angles, nA);
+}
+
+// Subsets of consecutive angles: [start, start + size).
+struct Block {
+    int start, size;
+};
+
+std::vector<Block> make_blocks(int nA, int bs) {
+    std::vector<Block> b;
+    for (int s = 0; s < nA; s += bs) b.push_back({s, (nA - s) < bs ? (nA - s) : bs});
+    return b;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) for the random block order.
+uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Shared body of SIRT and OS-SART (SIRT = one block holding every angle).
+tg_status sart_family(const tg_geometry *geo, const double *angles, int nA, const float *proj, float *vol,
+                      int niter, int blocksize, int order, uint64_t seed, float lambda, int nonneg,
+                      double *resid_hist, void *stream) {
+    tg_status st = check_common(geo, angles, nA);
+    if (st != TG_OK) return st;
+    if (niter < 0 || blocksize <= 0 || !vol || (nA > 0 && !proj)) return TG_ERR_ARG;
+    if (order != TG_ORDER_SEQUENTIAL && order != TG_ORDER_RANDOM) return TG_ERR_ARG;
+    if (!isfinite(lambda)) return TG_ERR_ARG;
+    if (niter == 0) return TG_OK;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nA);
+    Call c(stream);
+    View<const float> b = stage_in(c, proj, nray, true);
+    View<float> x = stage_in(c, vol, nvox, true);
+    const bool host_hist = resid_hist && is_host(resid_hist);
+    double *hist = resid_hist;
+    if (host_hist) {
+        hist = c.alloc<double>((size_t)niter);
+        c.sync_at_end = true;
+    }
+    if (nA == 0) {  // no data: the iterate does not move
+        if (hist && c.ok()) c.ok(cudaMemsetAsync(hist, 0, sizeof(double) * niter, c.s));
+        stage_out(c, x);
+        if (host_hist && c.ok())
+            c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+        return c.finish();
+    }
+    Angle *dA = upload_angles(c, geo, angles, nA);
+    const Grid g = call_grid(geo, angles, nA);
+    const auto blocks = make_blocks(nA, blocksize);
+    float *W = c.alloc<float>(nray);
+    float *r = c.alloc<float>(nray);
+    float *ones = c.alloc<float>(nvox > nray ? nvox : nray);
+    float *V = c.alloc<float>(nvox * blocks.size());
+    double *acc = c.alloc<double>(4);
+    unsigned int *amax = c.alloc<unsigned int>(1);
+    if (!c.ok()) return c.finish();
+    // W = 1 / (A 1) per ray, V_s = 1 / (A_s^T 1) per voxel and block.
+    c.ok(launch_fill(ones, 1.f, nvox > nray ? nvox : nray, c.s));
+    c.ok(launch_forward(TG_INTERP, g, dA, ones, W, 1, FP_STORE, FpEpilogue{}, c.s));
+    c.ok(launch_safe_inverse(W, nray, c.s));
+    const size_t plane = (size_t)g.nu * g.nv;
+    for (size_t k = 0; k < blocks.size() && c.ok(); ++k) {
+        Grid gs = g;
+        gs.nA = blocks[k].size;
+        // V and the updates below are divided voxel by voxel, so these
+        // backprojections keep FP32 accumulation (see tg_backproject.cu)
+        BpEpilogue e{};
+        e.scale = g.delta;
+        e.absmax = amax;
+        e.fp32_acc = 1;
+        c.ok(launch_backproject(TG_MATCHED, gs, dA + blocks[k].start, ones, V + k * nvox, 1, BP_STORE, e, c.s));
+        c.ok(launch_safe_inverse(V + k * nvox, nvox, c.s));
+    }
+    uint64_t rng = seed;
+    std::vector<int> perm(blocks.size());
+    for (int it = 0; it < niter && c.ok(); ++it) {
+        for (size_t k = 0; k < perm.size(); ++k) perm[k] = (int)k;
+        if (order == TG_ORDER_RANDOM)
+            for (size_t k = perm.size(); k > 1; --k) {
+                const size_t j = (size_t)(splitmix64(rng) % k);
+                int t = perm[k - 1];
+                perm[k - 1] = perm[j];
+                perm[j] = t;
+            }
+        for (size_t q = 0; q < perm.size() && c.ok(); ++q) {
+            const Block &B = blocks[perm[q]];
+            Grid gs = g;
+            gs.nA = B.size;
+            FpEpilogue fe{};
+            fe.b = b.dev + (size_t)B.start * plane;
+            fe.W = W + (size_t)B.start * plane;
+            c.ok(launch_forward(TG_INTERP, gs, dA + B.start, x.dev, r, 1, FP_RESID_W, fe, c.s));
+            BpEpilogue be{};
+            be.Vw = V + (size_t)perm[q] * nvox;
+            be.lambda = lambda;
+            be.nonneg = nonneg;
+            be.scale = g.delta;
+            be.absmax = amax;
+            be.fp32_acc = 1;
+            c.ok(launch_backproject(TG_MATCHED, gs, dA + B.start, r, x.dev, 1, BP_SIRT, be, c.s));
+        }
+        if (hist && c.ok()) {
+            c.ok(cudaMemsetAsync(acc, 0, sizeof(double), c.s));
+            FpEpilogue fe{};
+            fe.b = b.dev;
+            fe.norm = acc;
+            c.ok(launch_forward(TG_INTERP, g, dA, x.dev, r, 1, FP_RESID_NORM, fe, c.s));
+            c.ok(launch_sqrt_copy(acc, hist + it, c.s));
+        }
+    }
+    stage_out(c, x);
+    if (host_hist && c.ok())
+        c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+    return c.finish();
+}
+
+}  // namespace
+}  // namespace tg
+
+using namespace tg;
+
+extern "C" {
+
+const char *tg_status_string(tg_status s) {
+    switch (s) {
+        case TG_OK: return "ok";
+        case TG_ERR_ARG: return "invalid argument";
+        case TG_ERR_GEOMETRY: return "invalid geometry";
+        case TG_ERR_OOM: return "device out of memory";
+        case TG_ERR_CUDA: return "CUDA error";
+        case TG_ERR_TIMEOUT: return "device wait timed out";
+        case TG_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+uint64_t tg_launch_count(void) { return g_launches.load(); }
+
+tg_status tg_forward(const tg_geometry *geo, const double *angles, int nAngles, const float *vol, float *proj,
+                     int method, int batch, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (method != TG_INTERP && method != TG_SIDDON) return TG_ERR_ARG;
+    if (batch < 0) return TG_ERR_ARG;
+    if (nAngles == 0 || batch == 0) return TG_OK;
+    if (!vol || !proj) return TG_ERR_ARG;
+    const size_t nvox = vol_count(geo) * batch, nray = proj_count(geo, nAngles) * batch;
+    Call c(stream);
+    View<const float> v = stage_in(c, vol, nvox, true);
+    View<float> p = stage_in(c, proj, nray, false);
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    if (!c.ok()) return c.finish();
+    c.ok(launch_forward(method, make_grid(geo, nAngles), dA, v.dev, p.dev, batch, FP_STORE, FpEpilogue{}, c.s));
+    stage_out(c, p);
+    return c.finish();
+}
+
+tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                         float *vol, int method, int batch, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (method != TG_MATCHED && method != TG_FDK_WEIGHT) return TG_ERR_ARG;
+    if (batch < 0) return TG_ERR_ARG;
+    if (batch == 0) return TG_OK;
+    if (!vol || (nAngles > 0 && !proj)) return TG_ERR_ARG;
+    const size_t nvox = vol_count(geo) * batch, nray = proj_count(geo, nAngles) * batch;
+    Call c(stream);
+    View<float> v = stage_in(c, vol, nvox, false);
+    if (nAngles == 0) {
+        if (c.ok()) c.ok(cudaMemsetAsync(v.dev, 0, nvox * sizeof(float), c.s));
+        stage_out(c, v);
+        return c.finish();
+    }
+    View<const float> p = stage_in(c, proj, nray, true);
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    unsigned int *amax = c.alloc<unsigned int>((size_t)batch);
+    if (!c.ok()) return c.finish();
+    const Grid g = call_grid(geo, angles, nAngles);
+    BpEpilogue e{};
+    e.scale = method == TG_MATCHED ? g.delta : (float)(M_PI / nAngles);
+    e.absmax = amax;
+    c.ok(launch_backproject(method, g, dA, p.dev, v.dev, batch, BP_STORE, e, c.s));
+    stage_out(c, v);
+    return c.finish();
+}
+
+tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                 int filter, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (filter != TG_RAMLAK) return TG_ERR_ARG;
+    if (!vol || (nAngles > 0 && !proj)) return TG_ERR_ARG;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nAngles);
+    Call c(stream);
+    View<float> v = stage_in(c, vol, nvox, false);
+    if (nAngles == 0) {
+        if (c.ok()) c.ok(cudaMemsetAsync(v.dev, 0, nvox * sizeof(float), c.s));
+        stage_out(c, v);
+        return c.finish();
+    }
+    View<const float> p = stage_in(c, proj, nray, true);
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    float *filt = c.alloc<float>(nray);
+    if (!c.ok()) return c.finish();
+    const Grid g = call_grid(geo, angles, nAngles);
+    c.ok(launch_fdk_filter(g, dA, p.dev, filt, 1, c.s));
+    BpEpilogue e{};
+    e.scale = (float)(M_PI / nAngles);
+    if (c.ok()) c.ok(launch_backproject(TG_FDK_WEIGHT, g, dA, filt, v.dev, 1, BP_STORE, e, c.s));
+    stage_out(c, v);
+    return c.finish();
+}
+
+tg_status tg_sirt(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                  int niter, float lambda, int nonneg, double *resid_hist, void *stream) {
+    return sart_family(geo, angles, nAngles, proj, vol, niter, nAngles > 0 ? nAngles : 1, TG_ORDER_SEQUENTIAL, 0,
+                       lambda, nonneg, resid_hist, stream);
+}
+
+tg_status tg_ossart(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                    int niter, int blocksize, int order, uint64_t seed, float lambda, int nonneg,
+                    double *resid_hist, void *stream) {
+    return sart_family(geo, angles, nAngles, proj, vol, niter, blocksize, order, seed, lambda, nonneg,
+                       resid_hist, stream);
+}
+
+tg_status tg_cgls(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                  int niter, double *resid_hist, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (niter < 0 || !vol || (nAngles > 0 && !proj)) return TG_ERR_ARG;
+    if (niter == 0) return TG_OK;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nAngles);
+    Call c(stream);
+    View<const float> b = stage_in(c, proj, nray, true);
+    View<float> x = stage_in(c, vol, nvox, true);
+    const bool host_hist = resid_hist && is_host(resid_hist);
+    double *hist = resid_hist;
+    if (host_hist) {
+        hist = c.alloc<double>((size_t)niter);
+        c.sync_at_end = true;
+    }
+    if (nAngles == 0) {
+        if (hist && c.ok()) c.ok(cudaMemsetAsync(hist, 0, sizeof(double) * niter, c.s));
+        stage_out(c, x);
+        if (host_hist && c.ok())
+            c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+        return c.finish();
+    }
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    float *r = c.alloc<float>(nray);
+    float *q = c.alloc<float>(nray);
+    float *p = c.alloc<float>(nvox);
+    float *s = c.alloc<float>(nvox);
+    double *scal = c.alloc<double>(4);
+    unsigned int *amax = c.alloc<unsigned int>(1);
+    if (!c.ok()) return c.finish();
+    const Grid g = call_grid(geo, angles, nAngles);
+    // r = b - A x0 ; s = A^T r ; p = s ; gamma = ||s||^2
+    c.ok(launch_cgls_init(scal, c.s));
+    c.ok(launch_forward(TG_INTERP, g, dA, x.dev, r, 1, FP_STORE, FpEpilogue{}, c.s));
+    c.ok(launch_sub(b.dev, r, r, nray, c.s));
+    BpEpilogue be{};
+    be.scale = g.delta;
+    be.norm = scal + 2;
+    be.absmax = amax;
+    c.ok(launch_backproject(TG_MATCHED, g, dA, r, s, 1, BP_STORE_NORM, be, c.s));
+    c.ok(cudaMemcpyAsync(p, s, nvox * sizeof(float), cudaMemcpyDeviceToDevice, c.s));
+    c.ok(launch_cgls_rotate(scal, nullptr, c.s));
+    for (int it = 0; it < niter && c.ok(); ++it) {
+        FpEpilogue fe{};
+        fe.norm = scal + 1;
+        c.ok(launch_forward(TG_INTERP, g, dA, p, q, 1, FP_STORE_NORM, fe, c.s));      // q = A p
+        c.ok(launch_cgls_xr(x.dev, p, nvox, r, q, nray, scal, c.s));                  // x, r
+        c.ok(launch_backproject(TG_MATCHED, g, dA, r, s, 1, BP_STORE_NORM, be, c.s)); // s = A^T r
+        c.ok(launch_cgls_p(p, s, nvox, scal, c.s));                                   // p = s + beta p
+        c.ok(launch_cgls_rotate(scal, hist ? hist + it : nullptr, c.s));
+    }
+    stage_out(c, x);
+    if (host_hist && c.ok())
+        c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+    return c.finish();
+}
+
+tg_status tg_count_samples(const tg_geometry *geo, const double *angles, int nAngles, int method, uint64_t *count,
+                           void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (!count || (method != TG_INTERP && method != TG_SIDDON)) return TG_ERR_ARG;
+    *count = 0;
+    if (nAngles == 0) return TG_OK;
+    Call c(stream);
+    c.sync_at_end = true;
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    unsigned long long *d = c.alloc<unsigned long long>(1);
+    if (!c.ok()) return c.finish();
+    c.ok(cudaMemsetAsync(d, 0, sizeof(unsigned long long), c.s));
+    c.ok(launch_count(method, make_grid(geo, nAngles), dA, d, c.s));
+    unsigned long long h = 0;
+    c.ok(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+    tg_status out = c.finish();
+    if (out == TG_OK) *count = (uint64_t)h;
+    return out;
+}
+
+tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int batch, int blocksize,
+                            size_t *bytes) {
+    if (!geo || !bytes || nAngles < 0 || batch < 0) return TG_ERR_ARG;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nAngles);
+    const size_t ang = sizeof(Angle) * (size_t)(nAngles > 0 ? nAngles : 1) + 16;
+    size_t f = 0;
+    switch (op) {
+        case 0:
+        case 1: f = ang; break;
+        case 2: f = ang + 4 * nray + 16; break;
+        case 3:
+        case 4: {
+            const int bs = op == 3 ? (nAngles > 0 ? nAngles : 1) : blocksize;
+            if (bs <= 0) return TG_ERR_ARG;
+            const size_t nb = (size_t)((nAngles + bs - 1) / bs);
+            f = ang + 4 * (2 * nray + (nvox > nray ? nvox : nray) + nvox * nb) + 64;
+            break;
+        }
+        case 5: f = ang + 4 * (2 * nray + 2 * nvox) + 64; break;
+        default: return TG_ERR_ARG;
+    }
+    *bytes = f;
+    return TG_OK;
+}
+
+}  // extern "C"

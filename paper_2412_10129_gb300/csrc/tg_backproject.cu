@@ -1,0 +1,425 @@
+// tg_backproject.cu -- backprojectors.
+//
+// TG_MATCHED is the exact transpose of the interpolated projector (A^T in
+// the gradient step of TIGRE v3, Eq. 4): every sample k of every ray i adds
+// delta * y_i * w to the eight voxels its trilinear interpolation reads,
+// with the same weights w.
+//
+// It runs brick by brick.  A CTA owns a brick of BX x BY x BZ voxels and,
+// for every angle, visits the rays whose samples can touch it (the
+// detector bounding box of the brick grown by one voxel, the reach of a
+// trilinear footprint).  Each ray is rebuilt with the forward kernel's FP32
+// set-up, so the sample positions are bit-identical, and each sample
+// scatters its eight weighted contributions into shared memory.  Shared
+// float atomics are read-modify-write loops on this GPU, but 32-bit integer
+// atomics run at one warp instruction per clock, so the contributions are
+// accumulated in 32-bit fixed point: y is scaled so that no flush period
+// can overflow (the scale comes from max |y| over the call and a geometric
+// bound on one voxel's summed weights per projection), each product is
+// rounded to an integer with the 1.5 * 2^23 addend, and every FLUSH angles
+// the owned accumulators are converted and added to FP32 registers.
+// Integer sums do not depend on the order of the atomics, so the result is
+// deterministic; the rounding costs ~1e-6 of max |y| per product, random in
+// sign.  A warp's 32 rays are taken four pixels apart in u and v, so their
+// samples rarely share an accumulator (bank) in one instruction.  Only
+// bricks on the volume boundary need the rays' box-membership walk.
+//
+// TG_FDK_WEIGHT is the FDK backprojection (Sec. 2.1, direct methods):
+//     x_j = (pi / nAngles) sum_a (DSO / L_ja)^2 bilinear(p_a, u_ja, v_ja).
+#include "tg_internal.cuh"
+#include "tg_ray.cuh"
+
+namespace tg {
+
+namespace {
+
+__device__ __forceinline__ void block_add_bp(double v, double *dst) {
+    __shared__ double part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int warp = tid >> 5;
+    if (lane == 0) part[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+        for (int w = 0; w < nw; ++w) s += part[w];
+        atomicAdd(dst, s);
+    }
+    __syncthreads();  // part[] is reused by the next call
+}
+
+template <int MODE>
+__device__ __forceinline__ void bp_epilogue(float sum, bool valid, size_t vidx, size_t widx,
+                                            const BpEpilogue &ep, float *vol, int b) {
+    if (MODE == BP_STORE) {
+        if (valid) vol[vidx] = ep.scale * sum;
+    } else if (MODE == BP_SIRT) {
+        if (valid) {
+            float x = fmaf(ep.lambda * ep.Vw[widx], ep.scale * sum, vol[vidx]);
+            if (ep.nonneg) x = fmaxf(x, 0.f);
+            vol[vidx] = x;
+        }
+    } else {  // BP_STORE_NORM
+        const float s = ep.scale * sum;
+        if (valid) vol[vidx] = s;
+        const double d = valid ? (double)s : 0.0;
+        block_add_bp(d * d, ep.norm + b);
+    }
+}
+
+// max |y| per batch item (blockIdx.y), as the bit pattern of a non-negative
+// float (ordered like an unsigned int)
+__global__ void k_absmax(const float *__restrict__ y, size_t n, unsigned int *out) {
+    const float *yb = y + (size_t)blockIdx.y * n;
+    float m = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(yb[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, __float_as_uint(m));
+}
+
+// ---- matched transpose ------------------------------------------------------
+// Out of line: the membership walk is only taken on boundary bricks and
+// would otherwise crowd the registers of the scatter loop.
+__device__ __noinline__ bool ray_setup_outlined(const Angle &A, const Grid &g, int iu, int iv, Ray &r) {
+    return ray_setup(A, g, iu, iv, r);
+}
+
+constexpr int BX = 32, BY = 32, BZ = 16;              // owned voxels per brick
+constexpr int RX = BX + 2, RY = BY + 2, RZ = BZ + 2;  // with the one-voxel rim
+constexpr int PX = RX + 1;                            // row pitch (bank spreading)
+constexpr int PP = PX * RY + 9;                       // plane pitch
+constexpr int ACC_WORDS = PP * RZ;                    // one accumulator class
+constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4;       // bytes: two classes
+constexpr float FINE = 64.f;                          // scale ratio of the classes
+constexpr int MT = 512;                               // threads per CTA
+constexpr int OWN = BX * BY * BZ / MT;                // owned voxels per thread
+constexpr int FLUSH = 4;                              // angles per fixed-point period
+constexpr float MAGIC = 12582912.0f;                  // 1.5 * 2^23
+constexpr int MAGIC_BITS = 0x4B400000;
+static_assert(OWN == 32 && MT == 512 && BX == 32 && BY == 32, "owned-voxel map assumes these sizes");
+
+__device__ __forceinline__ unsigned int fixq(float v) {  // round(v) for |v| < 2^22
+    return (unsigned int)(__float_as_int(v + MAGIC) - MAGIC_BITS);
+}
+
+// F32: accumulate with FP32 shared atomics instead (read-modify-write loops,
+// ~2x slower here; the sums then depend on the order of the atomics at the
+// 1e-7 level).  Chosen where each voxel's sum must keep its own relative
+// precision however small it is -- SIRT and OS-SART divide it by the
+// voxel's column sum -- since fixed point rounds every product to a common
+// absolute step.
+template <int MODE, bool F32>
+__global__ void __launch_bounds__(MT, 1)
+    k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
+                 BpEpilogue ep, int nbx, int nby) {
+    extern __shared__ unsigned int acc[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = MT / 32;
+    const int bl = blockIdx.x, b = blockIdx.y;
+    const int bx = bl % nbx, by = (bl / nbx) % nby, bz = bl / (nbx * nby);
+    const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
+    // region of samples that can touch an owned voxel: p in [o - 1, o + B)
+    const float lox = (float)(x0 - 1), loy = (float)(y0 - 1), loz = (float)(z0 - 1);
+    const float hix = (float)(x0 + BX), hiy = (float)(y0 + BY), hiz = (float)(z0 + BZ);
+    const bool edge = x0 == 0 || y0 == 0 || z0 == 0 || x0 + BX >= g.nx || y0 + BY >= g.ny || z0 + BZ >= g.nz;
+    // Fixed-point scales: |contribution| <= lim, so |FLUSH-period sum| <=
+    // 2^30.  Rays with |y| <= max/FINE go to a second accumulator class with
+    // a FINE times finer scale, so that a few large rays (e.g. the heavily
+    // weighted corner rays of SIRT residuals) do not coarsen the others.
+    unsigned int *acc_f = acc + ACC_WORDS;
+    const float gmax = __uint_as_float(ep.absmax[b]);
+    const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
+    const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
+    const float inv_scale = scale > 0.f ? 1.f / scale : 0.f;
+    const float scale_f = FINE * scale, inv_scale_f = inv_scale * (1.f / FINE);
+    const float ybig = gmax * (1.f / FINE);
+    // owned voxel j of this thread: (lane, warp + 16 (j & 1), j >> 1)
+    const int obase = PP + (warp + 1) * PX + lane + 1;
+    float own[OWN];
+#pragma unroll
+    for (int j = 0; j < OWN; ++j) own[j] = 0.f;
+    for (int i = tid; i < 2 * ACC_WORDS; i += MT) acc[i] = 0u;
+    __syncthreads();
+    const float *pb = proj + (size_t)b * g.nA * g.nv * g.nu;
+    for (int a0 = 0; a0 < g.nA; a0 += FLUSH) {
+        const int a1 = min(a0 + FLUSH, g.nA);
+        for (int a = a0; a < a1; ++a) {
+            const Angle &A = angles[a];
+            // detector bounding box of the region's corners (mm frame)
+            float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float px = (((q & 1) ? hix : lox) + 0.5f - 0.5f * g.nx) * g.dx;
+                const float py = (((q & 2) ? hiy : loy) + 0.5f - 0.5f * g.ny) * g.dy;
+                const float pz = (((q & 4) ? hiz : loz) + 0.5f - 0.5f * g.nz) * g.dz;
+                const float L = fmaf(pz, A.n[2], fmaf(py, A.n[1], px * A.n[0])) - A.Sn;
+                const float Au = fmaf(pz, A.eu[2], fmaf(py, A.eu[1], px * A.eu[0])) - A.Seu;
+                const float Av = fmaf(pz, A.ev[2], fmaf(py, A.ev[1], px * A.ev[0])) - A.Sev;
+                const float iL = 1.f / L;
+                const float fu = fmaf(A.Ku * Au, iL, A.cu), fv = fmaf(A.Kv * Av, iL, A.cv);
+                umin = fminf(umin, fu);
+                umax = fmaxf(umax, fu);
+                vmin = fminf(vmin, fv);
+                vmax = fmaxf(vmax, fv);
+            }
+            const int u0 = max((int)ceilf(umin - 1e-3f), 0), u1 = min((int)floorf(umax + 1e-3f), g.nu - 1);
+            const int v0 = max((int)ceilf(vmin - 1e-3f), 0), v1 = min((int)floorf(vmax + 1e-3f), g.nv - 1);
+            if (u1 < u0 || v1 < v0) continue;
+            const float *pa = pb + (size_t)a * g.nv * g.nu;
+            // warp tasks: 32 x 16 pixel tiles, each split in 16 phases of
+            // 8 x 4 rays spaced four pixels apart
+            const int ntu = (u1 - u0 + 32) >> 5, ntv = (v1 - v0 + 16) >> 4;
+            const int ntask = ntu * ntv * 16;
+            for (int task = warp; task < ntask; task += nwarp) {
+                const int ph = task & 15, tile = task >> 4;
+                const int iu = u0 + (tile % ntu) * 32 + (lane & 7) * 4 + (ph & 3);
+                const int iv = v0 + (tile / ntu) * 16 + (lane >> 3) * 4 + (ph >> 2);
+                if (iu > u1 || iv > v1) continue;
+                const float yraw = __ldg(pa + (size_t)iv * g.nu + iu);
+                const bool big = fabsf(yraw) > ybig;
+                const float ys = F32 ? yraw : yraw * (big ? scale : scale_f);
+                unsigned int *const accc = big ? acc : acc_f;
+                Ray r;
+                int kb0 = 0, kb1 = 0x7fffffff;
+                if (edge) {
+                    if (!ray_setup_outlined(A, g, iu, iv, r)) continue;
+                    kb0 = r.k0;
+                    kb1 = r.k1;
+                } else {
+                    // the forward kernel's FP32 arithmetic for the sample positions
+                    const float fu = (float)iu, fv = (float)iv;
+                    const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
+                    const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
+                    const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
+                    const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float invL = rsqrtf(ss);
+                    const float f = g.delta * invL;
+                    r.sx = A.Sg[0];
+                    r.sy = A.Sg[1];
+                    r.sz = A.Sg[2];
+                    r.gx = dx * f * g.idx;
+                    r.gy = dy * f * g.idy;
+                    r.gz = dz * f * g.idz;
+                }
+                // samples of this ray inside the region
+                float klo = (float)kb0, khi = (float)kb1;
+                const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
+                const float lo[3] = {lox, loy, loz}, hi[3] = {hix, hiy, hiz};
+                bool miss = false;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (gv[ax] != 0.f) {
+                        const float ia = 1.f / gv[ax];
+                        const float ka = (lo[ax] - sv[ax]) * ia, kc = (hi[ax] - sv[ax]) * ia;
+                        klo = fmaxf(klo, fminf(ka, kc));
+                        khi = fminf(khi, fmaxf(ka, kc));
+                    } else if (sv[ax] < lo[ax] || sv[ax] >= hi[ax]) {
+                        miss = true;
+                    }
+                }
+                if (miss || !(khi >= klo)) continue;
+                const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
+                for (int k = ka; k <= kc; ++k) {
+                    const float kf = (float)k;
+                    const float x = fmaf(kf, r.gx, r.sx), yy = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
+                    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
+                    // local corner indices in the rimmed region: [0, R - 2]
+                    const int lx = (int)fx - (x0 - 1), ly = (int)fy - (y0 - 1), lz = (int)fz - (z0 - 1);
+                    if ((unsigned)lx > (unsigned)(RX - 2) || (unsigned)ly > (unsigned)(RY - 2) ||
+                        (unsigned)lz > (unsigned)(RZ - 2))
+                        continue;
+                    const float wx = x - fx, wy = yy - fy, wz = z - fz;
+                    const float c0 = ys * (1.f - wz), c1 = ys * wz;
+                    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
+                    const float ux = 1.f - wx;
+                    if (F32) {
+                        float *c = reinterpret_cast<float *>(acc) + lz * PP + ly * PX + lx;
+                        atomicAdd(c, b00 * ux);
+                        atomicAdd(c + 1, b00 * wx);
+                        atomicAdd(c + PX, b01 * ux);
+                        atomicAdd(c + PX + 1, b01 * wx);
+                        atomicAdd(c + PP, b10 * ux);
+                        atomicAdd(c + PP + 1, b10 * wx);
+                        atomicAdd(c + PP + PX, b11 * ux);
+                        atomicAdd(c + PP + PX + 1, b11 * wx);
+                    } else {
+                        unsigned int *c = accc + lz * PP + ly * PX + lx;
+                        atomicAdd(c, fixq(b00 * ux));
+                        atomicAdd(c + 1, fixq(b00 * wx));
+                        atomicAdd(c + PX, fixq(b01 * ux));
+                        atomicAdd(c + PX + 1, fixq(b01 * wx));
+                        atomicAdd(c + PP, fixq(b10 * ux));
+                        atomicAdd(c + PP + 1, fixq(b10 * wx));
+                        atomicAdd(c + PP + PX, fixq(b11 * ux));
+                        atomicAdd(c + PP + PX + 1, fixq(b11 * wx));
+                    }
+                }
+            }
+        }
+        // end of a fixed-point period: move the owned sums to FP32
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < OWN; ++j) {
+            const int o = obase + (j >> 1) * PP + (j & 1) * 16 * PX;
+            if (F32) {
+                float *af = reinterpret_cast<float *>(acc);
+                own[j] += af[o];
+                af[o] = 0.f;
+            } else {
+                const int v = (int)acc[o], vf = (int)acc_f[o];
+                acc[o] = 0u;
+                acc_f[o] = 0u;
+                own[j] += fmaf((float)v, inv_scale, (float)vf * inv_scale_f);
+            }
+        }
+        __syncthreads();
+    }
+    // owned voxels to the output
+    double part = 0.0;
+#pragma unroll
+    for (int j = 0; j < OWN; ++j) {
+        const int ix = x0 + lane, iy = y0 + warp + 16 * (j & 1), iz = z0 + (j >> 1);
+        const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
+        const size_t widx = ok ? ((size_t)iz * g.ny + iy) * g.nx + ix : 0;
+        const size_t vidx = (size_t)b * g.nx * g.ny * g.nz + widx;
+        if (MODE == BP_STORE_NORM) {
+            const float v = ep.scale * own[j];
+            if (ok) {
+                vol[vidx] = v;
+                part += (double)v * (double)v;
+            }
+        } else {
+            bp_epilogue<MODE>(own[j], ok, vidx, widx, ep, vol, b);
+        }
+    }
+    if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm + b);
+}
+
+// FDK-weighted backprojection; each thread owns a column of ZC voxels.
+constexpr int ZC = 8;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bp_fdk(const float *__restrict__ proj, float *__restrict__ vol,
+                                                const Angle *__restrict__ angles, Grid g, BpEpilogue ep,
+                                                int nzc) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
+    const bool valid = ix < g.nx && iy < g.ny;
+    const float mx = ((float)ix + 0.5f - 0.5f * g.nx) * g.dx;
+    const float my = ((float)iy + 0.5f - 0.5f * g.ny) * g.dy;
+    const int z0 = zc * ZC;
+    float mz[ZC], acc[ZC];
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        mz[k] = ((float)(z0 + k) + 0.5f - 0.5f * g.nz) * g.dz;
+        acc[k] = 0.f;
+    }
+    const float *pb = proj + (size_t)b * g.nA * g.nv * g.nu;
+    if (valid) {
+        for (int a = 0; a < g.nA; ++a) {
+            const Angle &A = angles[a];
+            const float *pa = pb + (size_t)a * g.nv * g.nu;
+            const float Lxy = fmaf(my, A.n[1], mx * A.n[0]) - A.Sn;
+            const float Uxy = fmaf(my, A.eu[1], mx * A.eu[0]) - A.Seu;
+            const float Vxy = fmaf(my, A.ev[1], mx * A.ev[0]) - A.Sev;
+#pragma unroll
+            for (int k = 0; k < ZC; ++k) {
+                const float L = fmaf(mz[k], A.n[2], Lxy);
+                const float Au = fmaf(mz[k], A.eu[2], Uxy);
+                const float Av = fmaf(mz[k], A.ev[2], Vxy);
+                const float iL = 1.f / L;
+                const float fu = fmaf(A.Ku * Au, iL, A.cu), fv = fmaf(A.Kv * Av, iL, A.cv);
+                const float w = A.DSO * iL;
+                const float ru = floorf(fu), rv = floorf(fv);
+                const float au = fu - ru, av = fv - rv;
+                const int iu = (int)ru, iv = (int)rv;
+                const bool u0 = iu >= 0 && iu < g.nu, u1 = iu + 1 >= 0 && iu + 1 < g.nu;
+                const bool v0 = iv >= 0 && iv < g.nv, v1 = iv + 1 >= 0 && iv + 1 < g.nv;
+                const long long o = (long long)iv * g.nu + iu;  // read only where in range
+                const float p00 = (u0 && v0) ? __ldg(pa + o) : 0.f;
+                const float p10 = (u1 && v0) ? __ldg(pa + o + 1) : 0.f;
+                const float p01 = (u0 && v1) ? __ldg(pa + o + g.nu) : 0.f;
+                const float p11 = (u1 && v1) ? __ldg(pa + o + g.nu + 1) : 0.f;
+                const float q0 = fmaf(au, p10 - p00, p00), q1 = fmaf(au, p11 - p01, p01);
+                acc[k] = fmaf(w * w, fmaf(av, q1 - q0, q0), acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const bool ok = valid && z0 + k < g.nz;
+        const size_t widx = ok ? ((size_t)(z0 + k) * g.ny + iy) * g.nx + ix : 0;
+        const size_t vidx = (size_t)b * g.nx * g.ny * g.nz + widx;
+        bp_epilogue<MODE>(acc[k], ok, vidx, widx, ep, vol, b);
+    }
+}
+
+template <int MODE, bool F32>
+cudaError_t launch_matched(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
+                           const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_bp_matched<MODE, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         MATCHED_SMEM);
+    if (e != cudaSuccess) return e;
+    k_bp_matched<MODE, F32><<<grid, MT, MATCHED_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles, const float *proj, float *vol,
+                               int batch, int mode, const BpEpilogue &ep, cudaStream_t s) {
+    if (batch == 0) return cudaSuccess;
+    if (method == TG_MATCHED) {
+        if (!ep.absmax || !(g.wbound > 0.f)) return cudaErrorInvalidValue;
+        const int nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY, nbz = (g.nz + BZ - 1) / BZ;
+        if (batch > 65535) return cudaErrorInvalidConfiguration;
+        const size_t n = (size_t)g.nA * g.nv * g.nu;  // per batch item
+        cudaError_t e = cudaMemsetAsync(ep.absmax, 0, sizeof(unsigned int) * batch, s);
+        if (e != cudaSuccess) return e;
+        if (n) {
+            size_t nb = (n + 255) / 256;
+            if (nb > 152 * 8) nb = 152 * 8;
+            k_absmax<<<dim3((unsigned)nb, batch), 256, 0, s>>>(proj, n, ep.absmax);
+            count_launch();
+        }
+        dim3 grid((unsigned)(nbx * nby * nbz), batch);
+        const bool f32 = ep.fp32_acc != 0;
+        switch (mode) {
+            case BP_STORE:
+                e = f32 ? launch_matched<BP_STORE, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                        : launch_matched<BP_STORE, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+                break;
+            case BP_SIRT:
+                e = f32 ? launch_matched<BP_SIRT, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                        : launch_matched<BP_SIRT, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+                break;
+            case BP_STORE_NORM:
+                e = f32 ? launch_matched<BP_STORE_NORM, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                        : launch_matched<BP_STORE_NORM, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    } else if (method == TG_FDK_WEIGHT) {
+        const int nzc = (g.nz + ZC - 1) / ZC;
+        dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8, nzc * batch);
+        if ((long long)nzc * batch > 65535) return cudaErrorInvalidConfiguration;
+        switch (mode) {
+            case BP_STORE: k_bp_fdk<BP_STORE><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
+            case BP_SIRT: k_bp_fdk<BP_SIRT><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
+            case BP_STORE_NORM: k_bp_fdk<BP_STORE_NORM><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tg

@@ -1,0 +1,413 @@
+// tg_forward.cu -- forward projectors A x (TIGRE v3, Eq. 1).
+//
+// Both kernels are ray driven: one thread per detector pixel.  A warp covers
+// an 8 x 4 pixel patch, so the 32 rays stay within a few voxels of each
+// other laterally and their trilinear gathers share cache lines.  The grid
+// runs u-blocks fastest, then angles, then detector-row blocks: the blocks in
+// flight at any time cover one band of rows (one z-slab of the volume) for
+// many angles, which keeps that slab resident in L2 while the angles sweep.
+#include <climits>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "tg_internal.cuh"
+#include "tg_ray.cuh"
+
+namespace tg {
+
+namespace {
+
+constexpr int BU = 32, BV = 8;  // pixels per block (u, v)
+
+__device__ __forceinline__ void pixel_of(int &iu, int &iv, int vb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    iu = blockIdx.x * BU + (warp & 3) * 8 + (lane & 7);
+    iv = vb * BV + (warp >> 2) * 4 + (lane >> 3);
+}
+
+// FP64 block reduction, one atomic per block.
+__device__ __forceinline__ void block_add(double v, double *dst) {
+    __shared__ double part[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) part[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        atomicAdd(dst, s);
+    }
+    __syncthreads();  // part[] may be reused
+}
+
+template <int MODE>
+__device__ __forceinline__ void fp_epilogue(float sum, bool valid, size_t pidx, size_t widx,
+                                            const FpEpilogue &ep, float *proj, int b) {
+    if (MODE == FP_STORE) {
+        if (valid) proj[pidx] = sum;
+    } else if (MODE == FP_RESID_W) {
+        if (valid) proj[pidx] = ep.W[widx] * (ep.b[pidx] - sum);
+    } else if (MODE == FP_STORE_NORM) {
+        if (valid) proj[pidx] = sum;
+        const double d = valid ? (double)sum : 0.0;
+        block_add(d * d, ep.norm + b);
+    } else {  // FP_RESID_NORM
+        const double d = valid ? (double)sum - (double)ep.b[pidx] : 0.0;
+        block_add(d * d, ep.norm + b);
+    }
+}
+
+// Interpolated projector: b_i = delta * sum_k trilinear(x, p_k).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fp_interp(const float *__restrict__ vol, float *__restrict__ proj,
+                                                   const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
+                                                   int nvb) {
+    const int a = blockIdx.y;
+    const int vb = blockIdx.z % nvb, b = blockIdx.z / nvb;
+    int iu, iv;
+    pixel_of(iu, iv, vb);
+    const bool valid = iu < g.nu && iv < g.nv;
+    const Angle &A = angles[a];
+    Ray r;
+    bool has = false;
+    if (valid) has = ray_setup(A, g, iu, iv, r);
+    const int k0 = has ? r.k0 : INT_MAX, k1 = has ? r.k1 : INT_MIN;
+    // Lanes step through the global sample index together, so that at any
+    // iteration the warp's samples lie at one distance from the source.
+    const int kw0 = __reduce_min_sync(0xffffffffu, k0);
+    const int kw1 = __reduce_max_sync(0xffffffffu, k1);
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const float *v = vol + (size_t)b * (size_t)nxy * nz;
+    float acc = 0.f;
+    for (int k = kw0; k <= kw1; ++k) {
+        if (k < k0 || k > k1) continue;
+        const float kf = (float)k;
+        const float x = fmaf(kf, r.gx, r.sx), y = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
+        const float fx = floorf(x), fy = floorf(y), fz = floorf(z);
+        const float wx = x - fx, wy = y - fy, wz = z - fz;
+        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        const bool x0 = ix >= 0, x1 = ix + 1 < nx;
+        const bool y0 = iy >= 0, y1 = iy + 1 < ny;
+        const bool z0 = iz >= 0, z1 = iz + 1 < nz;
+        const int base = (iz * ny + iy) * nx + ix;
+        const float c000 = (x0 && y0 && z0) ? __ldg(v + base) : 0.f;
+        const float c100 = (x1 && y0 && z0) ? __ldg(v + base + 1) : 0.f;
+        const float c010 = (x0 && y1 && z0) ? __ldg(v + base + nx) : 0.f;
+        const float c110 = (x1 && y1 && z0) ? __ldg(v + base + nx + 1) : 0.f;
+        const float c001 = (x0 && y0 && z1) ? __ldg(v + base + nxy) : 0.f;
+        const float c101 = (x1 && y0 && z1) ? __ldg(v + base + nxy + 1) : 0.f;
+        const float c011 = (x0 && y1 && z1) ? __ldg(v + base + nxy + nx) : 0.f;
+        const float c111 = (x1 && y1 && z1) ? __ldg(v + base + nxy + nx + 1) : 0.f;
+        const float c00 = fmaf(wx, c100 - c000, c000), c10 = fmaf(wx, c110 - c010, c010);
+        const float c01 = fmaf(wx, c101 - c001, c001), c11 = fmaf(wx, c111 - c011, c011);
+        const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
+        acc += fmaf(wz, c1 - c0, c0);
+    }
+    const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
+    const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
+    fp_epilogue<MODE>(acc * g.delta, valid, pidx, widx, ep, proj, b);
+}
+
+// Four texels of the 2 x 2 footprint around (u, v) in layer `layer` of a
+// layered 2-D texture (texture gather, first component).  Unnormalised
+// coordinates: texel i has its centre at i + 1/2, so u = i + 1 selects the
+// footprint {i, i + 1} exactly.  Returned raw, in the gather order
+// w = (i, j), z = (i+1, j), x = (i, j+1), y = (i+1, j+1); texels outside the
+// layer read as the zero border.
+__device__ __forceinline__ float4 gather4(cudaTextureObject_t t, int layer, float u, float v) {
+    float4 r;
+    asm("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(t), "r"(layer), "f"(u), "f"(v));
+    return r;
+}
+
+// Interpolated projector reading the volume through a layered texture (one
+// layer per z slice): two gathers fetch the eight trilinear corners, the
+// weights stay FP32 software (no hardware filtering).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, float *__restrict__ proj,
+                                                       const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
+                                                       int nvb, int b) {
+    const int a = blockIdx.y;
+    const int vb = blockIdx.z;
+    int iu, iv;
+    pixel_of(iu, iv, vb);
+    const bool valid = iu < g.nu && iv < g.nv;
+    const Angle &A = angles[a];
+    Ray r;
+    bool has = false;
+    if (valid) has = ray_setup(A, g, iu, iv, r);
+    const int k0 = has ? r.k0 : INT_MAX, k1 = has ? r.k1 : INT_MIN;
+    const int kw0 = __reduce_min_sync(0xffffffffu, k0);
+    const int kw1 = __reduce_max_sync(0xffffffffu, k1);
+    const int nz = g.nz;
+    float acc = 0.f;
+    for (int k = kw0; k <= kw1; ++k) {
+        if (k < k0 || k > k1) continue;
+        const float kf = (float)k;
+        const float x = fmaf(kf, r.gx, r.sx), y = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
+        const float fx = floorf(x), fy = floorf(y), fz = floorf(z);
+        const float wx = x - fx, wy = y - fy, wz = z - fz;
+        const int iz = (int)fz;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 lo = iz >= 0 ? gather4(tex, iz, fx + 1.f, fy + 1.f) : zero;
+        const float4 hi = iz + 1 < nz ? gather4(tex, iz + 1, fx + 1.f, fy + 1.f) : zero;
+        const float l0 = fmaf(wx, lo.z - lo.w, lo.w), l1 = fmaf(wx, lo.y - lo.x, lo.x);
+        const float h0 = fmaf(wx, hi.z - hi.w, hi.w), h1 = fmaf(wx, hi.y - hi.x, hi.x);
+        const float c0 = fmaf(wy, l1 - l0, l0), c1 = fmaf(wy, h1 - h0, h0);
+        acc += fmaf(wz, c1 - c0, c0);
+    }
+    const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
+    const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
+    fp_epilogue<MODE>(acc * g.delta, valid, pidx, widx, ep, proj, b);
+}
+
+// One layered array (and its texture object) per device and stream, grown
+// on demand and kept for the life of the process: launches on one stream
+// are ordered, so reusing it across calls on that stream is safe.
+struct TexCache {
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+    int nx = 0, ny = 0, nz = 0;
+};
+std::mutex g_tex_mu;
+std::map<std::pair<int, cudaStream_t>, TexCache> g_tex;
+
+bool texture_fits(const Grid &g) {
+    return g.nx <= 32768 && g.ny <= 32768 && g.nz <= 2048;
+}
+
+cudaError_t texture_for(const Grid &g, cudaStream_t s, TexCache &out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_tex_mu);
+    TexCache &c = g_tex[{dev, s}];
+    if (c.arr && (c.nx != g.nx || c.ny != g.ny || c.nz < g.nz)) {
+        // the old array may still be read by queued kernels of this stream
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        cudaDestroyTextureObject(c.tex);
+        cudaFreeArray(c.arr);
+        c = TexCache{};
+    }
+    if (!c.arr) {
+        cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+        e = cudaMalloc3DArray(&c.arr, &fd, make_cudaExtent(g.nx, g.ny, g.nz), cudaArrayLayered);
+        if (e != cudaSuccess) {
+            c = TexCache{};
+            return e;
+        }
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = c.arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = cudaAddressModeBorder;
+        td.addressMode[1] = cudaAddressModeBorder;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&c.tex, &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            cudaFreeArray(c.arr);
+            c = TexCache{};
+            return e;
+        }
+        c.nx = g.nx;
+        c.ny = g.ny;
+        c.nz = g.nz;
+    }
+    out = c;
+    return cudaSuccess;
+}
+
+cudaError_t copy_to_texture(const TexCache &c, const float *vol, const Grid &g, cudaStream_t s) {
+    cudaMemcpy3DParms p = {};
+    p.srcPtr = make_cudaPitchedPtr((void *)vol, (size_t)g.nx * sizeof(float), g.nx, g.ny);
+    p.dstArray = c.arr;
+    p.extent = make_cudaExtent(g.nx, g.ny, g.nz);
+    p.kind = cudaMemcpyDeviceToDevice;
+    return cudaMemcpy3DAsync(&p, s);
+}
+
+// Siddon projector: b_i = sum_j x_j |segment_i & cell_j|, incremental walk
+// over the cells the segment crosses.  Parameters are measured in mm from
+// the box entry point, so they stay small and keep FP32 resolution; each
+// crossing parameter is recomputed from its count with one FMA instead of
+// accumulated.
+// With COUNT the walk returns the number of cell segments it visits instead
+// of the line integral (the unit of work the benchmark reports).
+template <bool COUNT = false>
+__device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const Angle &A, const Grid &g,
+                                            int iu, int iv) {
+    const float fu = (float)iu, fv = (float)iv;
+    const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
+    const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
+    const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
+    const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float invL = rsqrtf(ss);
+    const float L = ss * invL;
+    // h = index + 1/2: cell i spans [i, i + 1); the box is [0, n] per axis.
+    const float S[3] = {A.Sg[0] + 0.5f, A.Sg[1] + 0.5f, A.Sg[2] + 0.5f};
+    const float D[3] = {dx * invL * g.idx, dy * invL * g.idy, dz * invL * g.idz};  // per mm
+    const int n[3] = {g.nx, g.ny, g.nz};
+    float tin = 0.f, tout = L;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (D[a] != 0.f) {
+            const float ia = __frcp_rn(D[a]);
+            const float ta = (0.f - S[a]) * ia, tb = ((float)n[a] - S[a]) * ia;
+            tin = fmaxf(tin, fminf(ta, tb));
+            tout = fminf(tout, fmaxf(ta, tb));
+        } else if (S[a] < 0.f || S[a] >= (float)n[a]) {
+            tout = -1.f;
+        }
+    }
+    if (!(tout > tin)) return 0.f;
+    int c[3], st[3];
+    float t0[3], dt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float h = fmaf(tin, D[a], S[a]);
+        if (D[a] > 0.f) {
+            c[a] = min(max((int)floorf(h), 0), n[a] - 1);
+            st[a] = 1;
+            dt[a] = __frcp_rn(D[a]);
+            t0[a] = ((float)(c[a] + 1) - h) * dt[a];
+        } else if (D[a] < 0.f) {
+            c[a] = min(max((int)ceilf(h) - 1, 0), n[a] - 1);
+            st[a] = -1;
+            dt[a] = -__frcp_rn(D[a]);
+            t0[a] = (h - (float)c[a]) * dt[a];
+        } else {
+            c[a] = (int)floorf(h);
+            st[a] = 0;
+            dt[a] = 0.f;
+            t0[a] = __int_as_float(0x7f800000);  // +inf: never crossed
+        }
+    }
+    const float tend = tout - tin;
+    int m[3] = {0, 0, 0};
+    float tn[3] = {t0[0], t0[1], t0[2]};
+    float tcur = 0.f, acc = 0.f;
+    const int nxy = g.nx * g.ny;
+    const int cap = g.nx + g.ny + g.nz + 4;
+    for (int it = 0; it < cap && tcur < tend; ++it) {
+        const float tnext = fminf(fminf(fminf(tn[0], tn[1]), tn[2]), tend);
+        if (c[0] >= 0 && c[0] < g.nx && c[1] >= 0 && c[1] < g.ny && c[2] >= 0 && c[2] < g.nz)
+            acc = COUNT ? acc + 1.f : fmaf(tnext - tcur, __ldg(v + c[2] * nxy + c[1] * g.nx + c[0]), acc);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (tn[a] == tnext) {
+                c[a] += st[a];
+                ++m[a];
+                tn[a] = fmaf((float)m[a], dt[a], t0[a]);
+            }
+        tcur = tnext;
+    }
+    return acc;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fp_siddon(const float *__restrict__ vol, float *__restrict__ proj,
+                                                   const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
+                                                   int nvb) {
+    const int a = blockIdx.y;
+    const int vb = blockIdx.z % nvb, b = blockIdx.z / nvb;
+    int iu, iv;
+    pixel_of(iu, iv, vb);
+    const bool valid = iu < g.nu && iv < g.nv;
+    const float *v = vol + (size_t)b * (size_t)g.nx * g.ny * g.nz;
+    const float sum = valid ? siddon_ray(v, angles[a], g, iu, iv) : 0.f;
+    const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
+    const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
+    fp_epilogue<MODE>(sum, valid, pidx, widx, ep, proj, b);
+}
+
+// Units of work of a forward projection: kept samples per ray (TG_INTERP)
+// or visited cell segments per ray (TG_SIDDON), summed over all rays.
+__global__ void __launch_bounds__(256) k_count(int method, const Angle *__restrict__ angles, Grid g, int nvb,
+                                               unsigned long long *out) {
+    const int a = blockIdx.y, vb = blockIdx.z;
+    int iu, iv;
+    pixel_of(iu, iv, vb);
+    unsigned long long n = 0;
+    if (iu < g.nu && iv < g.nv) {
+        if (method == TG_INTERP) {
+            Ray r;
+            if (ray_setup(angles[a], g, iu, iv, r)) n = (unsigned long long)(r.k1 - r.k0 + 1);
+        } else {
+            n = (unsigned long long)siddon_ray<true>(nullptr, angles[a], g, iu, iv);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(out, n);
+}
+
+}  // namespace
+
+cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsigned long long *out, cudaStream_t s) {
+    if (g.nA == 0) return cudaSuccess;
+    const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
+    if (nvb > 65535 || g.nA > 65535) return cudaErrorInvalidConfiguration;
+    k_count<<<dim3(nub, g.nA, nvb), 256, 0, s>>>(method, d_angles, g, nvb, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol, float *proj,
+                           int batch, int mode, const FpEpilogue &ep, cudaStream_t s) {
+    if (g.nA == 0 || batch == 0) return cudaSuccess;
+    const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
+    if ((long long)nvb * batch > 65535 || g.nA > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid(nub, g.nA, nvb * batch), block(256);
+    if (method == TG_INTERP && texture_fits(g)) {
+        TexCache tc;
+        cudaError_t e = texture_for(g, s, tc);
+        if (e != cudaSuccess) return e;
+        dim3 grid1(nub, g.nA, nvb);
+        const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+        for (int b = 0; b < batch; ++b) {
+            e = copy_to_texture(tc, vol + (size_t)b * nvox, g, s);
+            if (e != cudaSuccess) return e;
+            switch (mode) {
+                case FP_STORE: k_fp_interp_tex<FP_STORE><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
+                case FP_RESID_W: k_fp_interp_tex<FP_RESID_W><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
+                case FP_STORE_NORM: k_fp_interp_tex<FP_STORE_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
+                case FP_RESID_NORM: k_fp_interp_tex<FP_RESID_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
+                default: return cudaErrorInvalidValue;
+            }
+            count_launch();
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    } else if (method == TG_INTERP) {
+        // volumes beyond the layered-texture limits read global memory
+        switch (mode) {
+            case FP_STORE: k_fp_interp<FP_STORE><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_W: k_fp_interp<FP_RESID_W><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_STORE_NORM: k_fp_interp<FP_STORE_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_NORM: k_fp_interp<FP_RESID_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else if (method == TG_SIDDON) {
+        switch (mode) {
+            case FP_STORE: k_fp_siddon<FP_STORE><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_W: k_fp_siddon<FP_RESID_W><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_STORE_NORM: k_fp_siddon<FP_STORE_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_NORM: k_fp_siddon<FP_RESID_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tg

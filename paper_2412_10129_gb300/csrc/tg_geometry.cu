@@ -1,0 +1,250 @@
+// tg_geometry.cu -- host-side geometry: validation and per-projection
+// constants (TIGRE v3, Sec. 2.4; Appendix B parameter table).
+#include <math.h>
+#include <string.h>
+
+#include "tg_internal.cuh"
+
+namespace tg {
+
+namespace {
+
+struct Frame {
+    double S[3], D[3], eu[3], ev[3], n[3];
+};
+
+void rz(double a, double R[3][3]) {
+    double c = cos(a), s = sin(a);
+    double M[3][3] = {{c, -s, 0}, {s, c, 0}, {0, 0, 1}};
+    memcpy(R, M, sizeof(M));
+}
+void ry(double a, double R[3][3]) {
+    double c = cos(a), s = sin(a);
+    double M[3][3] = {{c, 0, s}, {0, 1, 0}, {-s, 0, c}};
+    memcpy(R, M, sizeof(M));
+}
+void rx(double a, double R[3][3]) {
+    double c = cos(a), s = sin(a);
+    double M[3][3] = {{1, 0, 0}, {0, c, -s}, {0, s, c}};
+    memcpy(R, M, sizeof(M));
+}
+void mul(const double A[3][3], const double B[3][3], double C[3][3]) {
+    double T[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) T[i][j] = A[i][0] * B[0][j] + A[i][1] * B[1][j] + A[i][2] * B[2][j];
+    memcpy(C, T, sizeof(T));
+}
+void apply(const double R[3][3], const double v[3], double o[3]) {
+    double t[3];
+    for (int i = 0; i < 3; ++i) t[i] = R[i][0] * v[0] + R[i][1] * v[1] + R[i][2] * v[2];
+    o[0] = t[0];
+    o[1] = t[1];
+    o[2] = t[2];
+}
+double dot(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+double at(const double *arr, int i, double dflt) { return arr ? arr[i] : dflt; }
+
+// The frame of projection a (conventions in include/tg.h).
+Frame frame(const tg_geometry *g, const double *angles, int a) {
+    const double DSO = at(g->DSO, a, g->DSO0), DSD = at(g->DSD, a, g->DSD0);
+    double S[3] = {DSO, 0, 0}, D[3] = {DSO - DSD, 0, 0};
+    const double u0[3] = {0, 1, 0}, v0[3] = {0, 0, 1};
+    double Rd[3][3], T[3][3];
+    rz(at(g->rotDetector, 3 * a + 0, 0.0), Rd);
+    ry(at(g->rotDetector, 3 * a + 1, 0.0), T);
+    mul(Rd, T, Rd);
+    rx(at(g->rotDetector, 3 * a + 2, 0.0), T);
+    mul(Rd, T, Rd);
+    double eu[3], ev[3];
+    apply(Rd, u0, eu);
+    apply(Rd, v0, ev);
+    const double ou = at(g->offDetector, 2 * a + 0, 0.0), ov = at(g->offDetector, 2 * a + 1, 0.0);
+    for (int i = 0; i < 3; ++i) D[i] += ou * eu[i] + ov * ev[i];
+    const double cor = at(g->COR, a, 0.0);
+    S[1] += cor;
+    D[1] += cor;
+    double R[3][3];
+    rz(angles[3 * a + 0], R);
+    ry(angles[3 * a + 1], T);
+    mul(R, T, R);
+    rz(angles[3 * a + 2], T);
+    mul(R, T, R);
+    Frame f;
+    apply(R, S, f.S);
+    apply(R, D, f.D);
+    apply(R, eu, f.eu);
+    apply(R, ev, f.ev);
+    for (int i = 0; i < 3; ++i) {
+        const double o = at(g->offOrigin, 3 * a + i, 0.0);
+        f.S[i] -= o;
+        f.D[i] -= o;
+    }
+    f.n[0] = -(f.eu[1] * f.ev[2] - f.eu[2] * f.ev[1]);
+    f.n[1] = -(f.eu[2] * f.ev[0] - f.eu[0] * f.ev[2]);
+    f.n[2] = -(f.eu[0] * f.ev[1] - f.eu[1] * f.ev[0]);
+    return f;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+tg_status validate_geometry(const tg_geometry *g, const double *angles, int nAngles) {
+    if (!g) return TG_ERR_ARG;
+    if (nAngles < 0) return TG_ERR_ARG;
+    if (nAngles > 0 && !angles) return TG_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (g->nVoxel[i] <= 0 || !finite_pos(g->dVoxel[i])) return TG_ERR_GEOMETRY;
+    for (int i = 0; i < 2; ++i)
+        if (g->nDetector[i] <= 0 || !finite_pos(g->dDetector[i])) return TG_ERR_GEOMETRY;
+    const double nvox = (double)g->nVoxel[0] * g->nVoxel[1] * g->nVoxel[2];
+    if (nvox >= 2147483647.0) return TG_ERR_UNSUPPORTED;  // int32 voxel indices
+    const double nray = (double)nAngles * g->nDetector[0] * g->nDetector[1];
+    if (nray >= 2147483647.0) return TG_ERR_UNSUPPORTED;
+    if (!(g->accuracy <= 0.0 || (isfinite(g->accuracy) && g->accuracy <= 64.0))) return TG_ERR_GEOMETRY;
+    const double h[3] = {0.5 * g->nVoxel[0] * g->dVoxel[0], 0.5 * g->nVoxel[1] * g->dVoxel[1],
+                         0.5 * g->nVoxel[2] * g->dVoxel[2]};
+    for (int a = 0; a < nAngles; ++a) {
+        const double DSO = at(g->DSO, a, g->DSO0), DSD = at(g->DSD, a, g->DSD0);
+        if (!finite_pos(DSO) || !finite_pos(DSD)) return TG_ERR_GEOMETRY;
+        for (int i = 0; i < 3; ++i)
+            if (!isfinite(angles[3 * a + i]) || !isfinite(at(g->offOrigin, 3 * a + i, 0.0)) ||
+                !isfinite(at(g->rotDetector, 3 * a + i, 0.0)))
+                return TG_ERR_GEOMETRY;
+        if (!isfinite(at(g->COR, a, 0.0)) || !isfinite(at(g->offDetector, 2 * a, 0.0)) ||
+            !isfinite(at(g->offDetector, 2 * a + 1, 0.0)))
+            return TG_ERR_GEOMETRY;
+        // The source must see the whole volume (grown by one voxel, the reach
+        // of the trilinear support) strictly in front of it, and the detector
+        // must lie beyond it: the voxel-driven backprojectors divide by the
+        // depth along the detector normal.
+        Frame f = frame(g, angles, a);
+        const double DSn = (f.D[0] - f.S[0]) * f.n[0] + (f.D[1] - f.S[1]) * f.n[1] + (f.D[2] - f.S[2]) * f.n[2];
+        if (!(DSn > 0.0)) return TG_ERR_GEOMETRY;
+        // The detector plane must also lie beyond that grown volume, so that
+        // no sample inside the volume lies past its pixel.
+        for (int q = 0; q < 8; ++q) {
+            double c[3];
+            for (int i = 0; i < 3; ++i) c[i] = ((q >> i) & 1 ? 1.0 : -1.0) * (h[i] + g->dVoxel[i]);
+            const double depth = (c[0] - f.S[0]) * f.n[0] + (c[1] - f.S[1]) * f.n[1] + (c[2] - f.S[2]) * f.n[2];
+            if (!(depth > 0.0) || !(depth < DSn)) return TG_ERR_GEOMETRY;
+        }
+    }
+    return TG_OK;
+}
+
+tg_status build_angles(const tg_geometry *g, const double *angles, int nAngles, Angle *out) {
+    const int nu = g->nDetector[0], nv = g->nDetector[1];
+    const double du = g->dDetector[0], dv = g->dDetector[1];
+    for (int a = 0; a < nAngles; ++a) {
+        Frame f = frame(g, angles, a);
+        Angle &A = out[a];
+        memset(&A, 0, sizeof(A));
+        const double su0 = (0.5 - 0.5 * nu) * du, sv0 = (0.5 - 0.5 * nv) * dv;
+        for (int i = 0; i < 3; ++i) {
+            A.S[i] = f.S[i];
+            A.P00[i] = f.D[i] + su0 * f.eu[i] + sv0 * f.ev[i];
+            A.U[i] = du * f.eu[i];
+            A.V[i] = dv * f.ev[i];
+            A.Sg[i] = (float)(f.S[i] / g->dVoxel[i] + 0.5 * g->nVoxel[i] - 0.5);
+            A.dir0[i] = (float)(A.P00[i] - f.S[i]);
+            A.Uf[i] = (float)A.U[i];
+            A.Vf[i] = (float)A.V[i];
+            A.n[i] = (float)f.n[i];
+            A.eu[i] = (float)f.eu[i];
+            A.ev[i] = (float)f.ev[i];
+        }
+        const double DS[3] = {f.D[0] - f.S[0], f.D[1] - f.S[1], f.D[2] - f.S[2]};
+        const double DSn = dot(DS, f.n);
+        A.Sn = (float)dot(f.S, f.n);
+        A.Seu = (float)dot(f.S, f.eu);
+        A.Sev = (float)dot(f.S, f.ev);
+        A.Ku = (float)(DSn / du);
+        A.Kv = (float)(DSn / dv);
+        A.cu = (float)(-dot(DS, f.eu) / du + 0.5 * nu - 0.5);
+        A.cv = (float)(-dot(DS, f.ev) / dv + 0.5 * nv - 0.5);
+        const double DSO = at(g->DSO, a, g->DSO0), DSD = at(g->DSD, a, g->DSD0);
+        A.DSO = (float)DSO;
+        A.tau = (float)(du * DSO / DSD);
+    }
+    return TG_OK;
+}
+
+// A voxel's trilinear support is a cube of side 2 d.  One ray keeps at most
+// 2 sqrt(3) max(d) / delta + 1 samples in it, each with weight <= 1; the
+// rays through it are those whose pixels lie in its shadow, whose diameter
+// is at most 2 sqrt(3) max(d) times the largest magnification DSD_n / L over
+// the (one-voxel grown) volume, in pixels of min(du, dv), times the largest
+// obliquity |P - S| / DSD_n of a detector corner ray (a tilted ray stretches
+// the shadow), times 1.1 for margin.
+void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles, Grid &g) {
+    double dmax = geo->dVoxel[0];
+    if (geo->dVoxel[1] > dmax) dmax = geo->dVoxel[1];
+    if (geo->dVoxel[2] > dmax) dmax = geo->dVoxel[2];
+    const double pmin = geo->dDetector[0] < geo->dDetector[1] ? geo->dDetector[0] : geo->dDetector[1];
+    const double h[3] = {0.5 * geo->nVoxel[0] * geo->dVoxel[0] + geo->dVoxel[0],
+                         0.5 * geo->nVoxel[1] * geo->dVoxel[1] + geo->dVoxel[1],
+                         0.5 * geo->nVoxel[2] * geo->dVoxel[2] + geo->dVoxel[2]};
+    double mag = 0.0, obl = 1.0;
+    for (int a = 0; a < nAngles; ++a) {
+        Frame f = frame(geo, angles, a);
+        const double DSn = (f.D[0] - f.S[0]) * f.n[0] + (f.D[1] - f.S[1]) * f.n[1] + (f.D[2] - f.S[2]) * f.n[2];
+        for (int q = 0; q < 4; ++q) {
+            const double su = ((q & 1) ? 0.5 : -0.5) * geo->nDetector[0] * geo->dDetector[0];
+            const double sv = ((q & 2) ? 0.5 : -0.5) * geo->nDetector[1] * geo->dDetector[1];
+            double r2 = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                const double c = f.D[i] + su * f.eu[i] + sv * f.ev[i] - f.S[i];
+                r2 += c * c;
+            }
+            if (sqrt(r2) / DSn > obl) obl = sqrt(r2) / DSn;
+        }
+        for (int q = 0; q < 8; ++q) {
+            double depth = 0.0;
+            for (int i = 0; i < 3; ++i) depth += (((q >> i) & 1 ? 1.0 : -1.0) * h[i] - f.S[i]) * f.n[i];
+            if (depth > 0.0 && DSn / depth > mag) mag = DSn / depth;
+        }
+    }
+    const double per_ray = 2.0 * sqrt(3.0) * dmax / g.delta64 + 1.0;
+    const double width = 1.1 * obl * 2.0 * sqrt(3.0) * dmax * mag / pmin + 2.0;
+    g.wbound = (float)(per_ray * width * width);
+}
+
+Grid make_grid(const tg_geometry *geo, int nAngles) {
+    Grid g;
+    memset(&g, 0, sizeof(g));
+    g.nx = geo->nVoxel[0];
+    g.ny = geo->nVoxel[1];
+    g.nz = geo->nVoxel[2];
+    g.nu = geo->nDetector[0];
+    g.nv = geo->nDetector[1];
+    g.nA = nAngles;
+    g.dx = (float)geo->dVoxel[0];
+    g.dy = (float)geo->dVoxel[1];
+    g.dz = (float)geo->dVoxel[2];
+    g.idx = (float)(1.0 / geo->dVoxel[0]);
+    g.idy = (float)(1.0 / geo->dVoxel[1]);
+    g.idz = (float)(1.0 / geo->dVoxel[2]);
+    g.idx64 = 1.0 / geo->dVoxel[0];
+    g.idy64 = 1.0 / geo->dVoxel[1];
+    g.idz64 = 1.0 / geo->dVoxel[2];
+    g.hx64 = 0.5 * geo->nVoxel[0] * geo->dVoxel[0];
+    g.hy64 = 0.5 * geo->nVoxel[1] * geo->dVoxel[1];
+    g.hz64 = 0.5 * geo->nVoxel[2] * geo->dVoxel[2];
+    g.hx = (float)g.hx64;
+    g.hy = (float)g.hy64;
+    g.hz = (float)g.hz64;
+    double dmin = geo->dVoxel[0];
+    if (geo->dVoxel[1] < dmin) dmin = geo->dVoxel[1];
+    if (geo->dVoxel[2] < dmin) dmin = geo->dVoxel[2];
+    const double acc = geo->accuracy > 0.0 ? geo->accuracy : 0.5;
+    g.delta64 = acc * dmin;
+    g.delta = (float)g.delta64;
+    g.inv_delta = (float)(1.0 / g.delta64);
+    g.du = (float)geo->dDetector[0];
+    g.dv = (float)geo->dDetector[1];
+    return g;
+}
+
+}  // namespace tg

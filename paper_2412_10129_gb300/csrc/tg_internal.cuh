@@ -1,0 +1,123 @@
+// tg_internal.cuh -- shared device/host definitions of libtg (not part of the ABI).
+//
+// Coordinates.  Geometry arrives in millimetres in the volume-centred frame
+// (TIGRE v3, Sec. 2.4 and the Appendix B parameter table).  The kernels
+// work in voxel index space: g = p / d + n / 2 - 1/2, so voxel i has its
+// centre at g = i and the closed volume box is [-1/2, n - 1/2] per axis.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tg.h"
+
+namespace tg {
+
+// Per-projection constants, built on the host in FP64 (tg_geometry.cu).
+struct alignas(16) Angle {
+    // FP64 frame (mm, volume-centred): used for exact box-membership
+    // decisions of the interpolated projector's samples.
+    double S[3];    // source
+    double P00[3];  // centre of pixel (0, 0)
+    double U[3];    // du * eu
+    double V[3];    // dv * ev
+    // FP32 copies for the sampling loops.
+    float Sg[3];    // source in index space
+    float dir0[3];  // P00 - S (mm)
+    float Uf[3];    // du * eu (mm)
+    float Vf[3];    // dv * ev (mm)
+    // FDK pieces (mm frame): L = c.n - S.n, Au = c.eu - S.eu, Av = c.ev - S.ev,
+    // fu = cu + Ku Au / L, fv = cv + Kv Av / L, weight (DSO / L)^2.
+    float n[3], eu[3], ev[3];
+    float Sn, Seu, Sev;
+    float Ku, Kv, cu, cv;
+    float DSO;
+    float tau;      // Ram-Lak sampling distance du * DSO / DSD (mm)
+    float pad[2];
+};
+
+// Volume / detector description shared by all kernels of a call.
+struct Grid {
+    int nx, ny, nz;
+    int nu, nv;
+    int nA;             // angles of this launch
+    float dx, dy, dz;   // mm
+    float idx, idy, idz;  // 1 / d
+    float hx, hy, hz;   // half extents (mm)
+    float delta;        // interpolated step (mm)
+    float inv_delta;
+    double delta64;
+    double hx64, hy64, hz64;
+    double idx64, idy64, idz64;
+    float du, dv;
+    // Upper bound of the summed trilinear weights one voxel can receive from
+    // one projection (matched backprojector fixed-point range).
+    float wbound;
+};
+
+// Epilogue modes of the forward projector.
+enum FpMode {
+    FP_STORE = 0,     // proj = A x
+    FP_RESID_W = 1,   // proj = W (b - A x)               (SIRT / OS-SART)
+    FP_STORE_NORM = 2,// proj = A x, norm += ||A x||^2     (CGLS q = A p)
+    FP_RESID_NORM = 3 // norm += ||A x - b||^2, no store   (residual history)
+};
+
+// Epilogue modes of the backprojectors.
+enum BpMode {
+    BP_STORE = 0,      // vol = scale * A^T y
+    BP_SIRT = 1,       // vol = clamp(vol + lambda V A^T y)
+    BP_STORE_NORM = 2  // vol = A^T y, norm += ||A^T y||^2 (CGLS s = A^T r)
+};
+
+struct FpEpilogue {
+    const float *b;      // measured data (FP_RESID_*), same layout as proj
+    const float *W;      // per-ray weight (FP_RESID_W), [nA][nv][nu], shared across batch
+    double *norm;        // FP64 accumulator (one per batch item)
+};
+
+struct BpEpilogue {
+    const float *Vw;     // per-voxel weight (BP_SIRT), [nz][ny][nx]
+    float lambda;
+    int nonneg;
+    float scale;         // BP_STORE multiplier
+    double *norm;        // FP64 accumulator (one per batch item)
+    unsigned int *absmax;  // device scratch words (TG_MATCHED: max |y| per batch item)
+    int fp32_acc;          // TG_MATCHED: accumulate in FP32 (per-voxel relative precision)
+};
+
+// Host helpers (tg_geometry.cu).
+tg_status build_angles(const tg_geometry *geo, const double *angles, int nAngles, Angle *out);
+tg_status validate_geometry(const tg_geometry *geo, const double *angles, int nAngles);
+Grid make_grid(const tg_geometry *geo, int nAngles);
+// Fills g.wbound for the given projections (see Grid::wbound).
+void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles, Grid &g);
+
+// Launch bookkeeping (tg_api.cu).
+void count_launch(uint64_t n = 1);
+
+// Kernel launchers (each returns cudaGetLastError()).
+cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol,
+                           float *proj, int batch, int mode, const FpEpilogue &ep, cudaStream_t s);
+cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles, const float *proj,
+                               float *vol, int batch, int mode, const BpEpilogue &ep,
+                               cudaStream_t s);
+cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsigned long long *out,
+                         cudaStream_t s);
+cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const float *proj, float *out,
+                              int batch, cudaStream_t s);
+
+// Vector kernels (tg_vector.cu).
+cudaError_t launch_safe_inverse(float *a, size_t n, cudaStream_t s);
+cudaError_t launch_fill(float *a, float v, size_t n, cudaStream_t s);
+cudaError_t launch_sub(const float *a, const float *b, float *out, size_t n, cudaStream_t s);
+cudaError_t launch_norm2(const float *a, size_t n, double *acc, cudaStream_t s);
+// CGLS steps; scal = device FP64 scalars [gamma, qq, gamma_new, ...].
+cudaError_t launch_cgls_xr(float *x, const float *p, size_t nvox, float *r, const float *q,
+                           size_t nray, double *scal, cudaStream_t s);
+cudaError_t launch_cgls_p(float *p, const float *sv, size_t nvox, double *scal, cudaStream_t s);
+cudaError_t launch_cgls_rotate(double *scal, double *hist_slot, cudaStream_t s);
+cudaError_t launch_cgls_init(double *scal, cudaStream_t s);
+cudaError_t launch_sqrt_copy(const double *src, double *dst, cudaStream_t s);
+
+}  // namespace tg

@@ -1,0 +1,166 @@
+// tg_vector.cu -- element-wise and reduction kernels of the iterative
+// solvers: SIRT weights (row and column sums inverted, 0 where the sum is 0)
+// and the CGLS vector updates (Hestenes-Stiefel), whose inner products are
+// accumulated in FP64.  The CGLS scalars live in device memory, so an
+// iteration never waits on the host.
+//
+// CGLS scalar slots: s[0] gamma = ||s||^2, s[1] ||q||^2, s[2] gamma' (next
+// ||s||^2), s[3] ||r||^2.
+#include "tg_internal.cuh"
+
+namespace tg {
+
+namespace {
+
+constexpr int TPB = 256;
+
+int blocks_for(size_t n) {
+    size_t b = (n + TPB - 1) / TPB;
+    const size_t cap = 152 * 16;  // grid-stride beyond a few waves
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+__device__ __forceinline__ void block_sum(double v, double *dst) {
+    __shared__ double part[TPB / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < TPB / 32; ++w) s += part[w];
+        atomicAdd(dst, s);
+    }
+}
+
+__global__ void k_safe_inverse(float *a, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const float v = a[i];
+        a[i] = v != 0.f ? 1.f / v : 0.f;
+    }
+}
+
+__global__ void k_fill(float *a, float v, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) a[i] = v;
+}
+
+__global__ void k_sub(const float *a, const float *b, float *o, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) o[i] = a[i] - b[i];
+}
+
+__global__ void k_norm2(const float *a, size_t n, double *acc) {
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const double v = a[i];
+        s += v * v;
+    }
+    block_sum(s, acc);
+}
+
+// x += alpha p ; r -= alpha q ; s[3] += ||r||^2 with alpha = gamma / ||q||^2.
+__global__ void k_cgls_xr(float *x, const float *p, size_t nvox, float *r, const float *q, size_t nray,
+                          double *s) {
+    const double qq = s[1];
+    const float alpha = qq > 0.0 ? (float)(s[0] / qq) : 0.f;
+    const size_t n = nvox > nray ? nvox : nray;
+    double rr = 0.0;
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        if (i < nvox) x[i] = fmaf(alpha, p[i], x[i]);
+        if (i < nray) {
+            const float v = fmaf(-alpha, q[i], r[i]);
+            r[i] = v;
+            rr += (double)v * (double)v;
+        }
+    }
+    block_sum(rr, s + 3);
+}
+
+// p = s + beta p with beta = gamma' / gamma.
+__global__ void k_cgls_p(float *p, const float *sv, size_t nvox, const double *s) {
+    const double g = s[0];
+    const float beta = g > 0.0 ? (float)(s[2] / g) : 0.f;
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < nvox; i += (size_t)gridDim.x * TPB)
+        p[i] = fmaf(beta, p[i], sv[i]);
+}
+
+// gamma <- gamma'; history slot <- ||r||; clear the accumulators.
+__global__ void k_cgls_rotate(double *s, double *hist_slot) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (hist_slot) *hist_slot = sqrt(s[3]);
+        s[0] = s[2];
+        s[1] = 0.0;
+        s[2] = 0.0;
+        s[3] = 0.0;
+    }
+}
+
+__global__ void k_zero4(double *s) {
+    if (threadIdx.x < 4) s[threadIdx.x] = 0.0;
+}
+
+__global__ void k_sqrt_copy(const double *src, double *dst) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = sqrt(*src);
+}
+
+}  // namespace
+
+cudaError_t launch_safe_inverse(float *a, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_safe_inverse<<<blocks_for(n), TPB, 0, s>>>(a, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float *a, float v, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_fill<<<blocks_for(n), TPB, 0, s>>>(a, v, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub(const float *a, const float *b, float *out, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_sub<<<blocks_for(n), TPB, 0, s>>>(a, b, out, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(const float *a, size_t n, double *acc, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_norm2<<<blocks_for(n), TPB, 0, s>>>(a, n, acc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cgls_xr(float *x, const float *p, size_t nvox, float *r, const float *q, size_t nray,
+                           double *scal, cudaStream_t s) {
+    k_cgls_xr<<<blocks_for(nvox > nray ? nvox : nray), TPB, 0, s>>>(x, p, nvox, r, q, nray, scal);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cgls_p(float *p, const float *sv, size_t nvox, double *scal, cudaStream_t s) {
+    k_cgls_p<<<blocks_for(nvox), TPB, 0, s>>>(p, sv, nvox, scal);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cgls_rotate(double *scal, double *hist_slot, cudaStream_t s) {
+    k_cgls_rotate<<<1, 32, 0, s>>>(scal, hist_slot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cgls_init(double *scal, cudaStream_t s) {
+    k_zero4<<<1, 32, 0, s>>>(scal);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sqrt_copy(const double *src, double *dst, cudaStream_t s) {
+    k_sqrt_copy<<<1, 32, 0, s>>>(src, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tg

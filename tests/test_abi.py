@@ -1,0 +1,111 @@
+"""The C ABI: libtg builds, loads and exports every function include/tg.h
+declares; host-side argument and geometry validation runs before any CUDA
+call, so it is checked here without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2412_10129_gb300 import build, inputs, tg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return tg.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("tg_forward", "tg_backproject", "tg_fdk", "tg_sirt", "tg_ossart", "tg_cgls",
+              "tg_workspace_size", "tg_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    assert tg.status_string(0) == "ok"
+    assert tg.status_string(2) == "invalid geometry"
+    assert "unknown" in tg.status_string(99)
+
+
+def _geo():
+    return inputs.circular_geometry((8, 8, 8), (1.0,) * 3, (10, 10), (1.5, 1.5), 4, 100.0, 160.0)
+
+
+def _call_forward(geo, vol=None, proj=None, method=0, batch=1):
+    G = tg._Geo(geo)
+    v = vol if vol is not None else np.zeros(geo.vol_shape, np.float32)
+    p = proj if proj is not None else np.zeros(geo.proj_shape, np.float32)
+    return tg.load().tg_forward(G.ref, G.ang, G.n, v.ctypes.data, p.ctypes.data, method, batch, None)
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda g: setattr(g, "nVoxel", (0, 8, 8)), 2),
+    (lambda g: setattr(g, "dVoxel", (1.0, -1.0, 1.0)), 2),
+    (lambda g: setattr(g, "nDetector", (10, 0)), 2),
+    (lambda g: setattr(g, "dDetector", (float("nan"), 1.0)), 2),
+    (lambda g: setattr(g, "DSO", np.full(4, -5.0)), 2),
+    (lambda g: setattr(g, "DSD", np.full(4, 0.0)), 2),
+    # source inside the volume
+    (lambda g: setattr(g, "DSO", np.full(4, 3.0)), 2),
+    # detector plane cutting through the volume
+    (lambda g: setattr(g, "DSD", np.full(4, 101.0)), 2),
+    (lambda g: g.angles.__setitem__((1, 0), float("inf")), 2),
+])
+def test_invalid_geometry_is_rejected_on_the_host(lib, mutate, code):
+    g = _geo()
+    mutate(g)
+    assert _call_forward(g) == code
+
+
+def test_invalid_arguments_are_rejected(lib):
+    g = _geo()
+    G = tg._Geo(g)
+    p = np.zeros(g.proj_shape, np.float32)
+    assert lib.tg_forward(G.ref, G.ang, G.n, None, p.ctypes.data, 0, 1, None) == 1
+    assert _call_forward(g, method=7) == 1
+    assert _call_forward(g, batch=-1) == 1
+    assert lib.tg_forward(None, G.ang, G.n, None, None, 0, 1, None) == 1
+    assert lib.tg_forward(G.ref, None, 3, None, None, 0, 1, None) == 1
+    v = np.zeros(g.vol_shape, np.float32)
+    assert lib.tg_backproject(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 5, 1, None) == 1
+    assert lib.tg_fdk(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 3, None) == 1
+    assert lib.tg_sirt(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, -1, 1.0, 1, None, None) == 1
+    assert lib.tg_ossart(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 2, 0, 0, 0, 1.0, 1, None, None) == 1
+    assert lib.tg_ossart(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 2, 2, 9, 0, 1.0, 1, None, None) == 1
+    assert lib.tg_cgls(G.ref, G.ang, G.n, p.ctypes.data, None, 2, None, None) == 1
+
+
+def test_empty_requests_are_no_ops(lib):
+    """nAngles == 0 or batch == 0 returns before touching the device."""
+    g = _geo()
+    G = tg._Geo(g)
+    assert lib.tg_forward(G.ref, G.ang, 0, None, None, 0, 1, None) == 0
+    assert lib.tg_forward(G.ref, G.ang, G.n, None, None, 0, 0, None) == 0
+    assert lib.tg_backproject(G.ref, G.ang, G.n, None, None, 0, 0, None) == 0
+    one = np.zeros(1, np.float32)
+    assert lib.tg_cgls(G.ref, G.ang, G.n, one.ctypes.data, one.ctypes.data, 0, None, None) == 0
+    assert lib.tg_sirt(G.ref, G.ang, G.n, one.ctypes.data, one.ctypes.data, 0, 1.0, 1, None, None) == 0
+
+
+def test_workspace_size(lib):
+    g = inputs.config_clinical()
+    nvox, nray = 512 ** 3, 720 * 768 * 1024
+    assert tg.workspace_size(g, "cgls") >= 4 * (2 * nray + 2 * nvox)
+    assert tg.workspace_size(g, "ossart", blocksize=20) >= 4 * nvox * 36
+    assert tg.workspace_size(g, "forward") < 1 << 20
