@@ -106,6 +106,26 @@ tg_status tg_forward(const tg_geometry *geo, const double *angles, int nAngles, 
 tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngles,
                          const float *proj, float *vol, int method, int batch, void *stream);
 
+/* tg_backproject for callers that cannot allocate device memory (the paper
+ * has no counterpart: this is a deployment variant).  Some callers cannot
+ * call cudaMalloc when they backproject -- code running while a CUDA graph
+ * is built around it, hosts that fix their device memory budget at start-up,
+ * latency-bound real-time paths -- so this call allocates nothing, neither
+ * device nor host heap memory.  Same arguments and results as
+ * tg_backproject, with these limits:
+ *   - proj and vol must be device (or managed) memory; host buffers return
+ *     TG_ERR_ARG (staging them would need an allocation);
+ *   - nAngles <= 4096 and batch <= 256, else TG_ERR_UNSUPPORTED;
+ *   - its scratch (per-angle constants and one word per batch item, under
+ *     1 MiB) is one static device array that every GPU loading the library
+ *     holds until the process exits.  The first call on a device looks the
+ *     array's address up (cudaGetSymbolAddress) for that device; make that
+ *     first call before any stream capture.  Every call reuses the same
+ *     array, so calls that overlap on the GPU (other streams, other host
+ *     threads) race: serialise them, e.g. on one stream. */
+tg_status tg_backproject_noalloc(const tg_geometry *geo, const double *angles, int nAngles,
+                                 const float *proj, float *vol, int method, int batch, void *stream);
+
 /* FDK (Sec. 2.1, direct methods): cosine pre-weight |(P-S).n|/|P-S|, Ram-Lak
  * row filter sampled at du*DSO/DSD (linear convolution, no wrap-around),
  * TG_FDK_WEIGHT backprojection.  Assumes equally spaced angles over 2 pi.

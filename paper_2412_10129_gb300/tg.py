@@ -73,6 +73,7 @@ def load():
             "tg_workspace_size": [G, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_size_t)],
             "tg_count_samples": [G, _DP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _VP],
+            "tg_backproject_noalloc": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -185,6 +186,21 @@ def backproject(geo, proj, method: str = "matched", out=None, stream=None):
         out = _empty_like_kind(proj, shape)
     _check("tg_backproject", load().tg_backproject(G.ref, G.ang, G.n, _ptr(proj), _ptr(out), _METHOD_BP[method], B,
                                                    _stream(proj, stream)))
+    return out
+
+
+def backproject_noalloc(geo, proj, method: str = "matched", out=None, stream=None):
+    """tg_backproject_noalloc: the backprojection for callers that cannot
+    allocate device memory.  ``proj`` (and ``out``, if given) must be CUDA
+    tensors; the library allocates nothing (its scratch is a static device
+    array), so calls that overlap on the GPU must be serialised."""
+    G = _Geo(geo)
+    B, batched = _batch(proj, 3)
+    shape = ((B,) if batched else ()) + tuple(geo.vol_shape)
+    if out is None:
+        out = _empty_like_kind(proj, shape)
+    _check("tg_backproject_noalloc", load().tg_backproject_noalloc(G.ref, G.ang, G.n, _ptr(proj), _ptr(out),
+                                                                   _METHOD_BP[method], B, _stream(proj, stream)))
     return out
 
 
