@@ -223,17 +223,25 @@ __global__ void __launch_bounds__(MT, 1)
                 }
                 if (miss || !(khi >= klo)) continue;
                 const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
+                // Branch-free body, two samples per trip for instruction-level
+                // parallelism.  A sample whose cell falls outside the rimmed
+                // region (FP32 rounding at the region's edge; its weights on
+                // owned voxels are zero) is clamped into it and adds zeros.
+#pragma unroll 2
                 for (int k = ka; k <= kc; ++k) {
                     const float kf = (float)k;
                     const float x = fmaf(kf, r.gx, r.sx), yy = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
                     const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
                     // local corner indices in the rimmed region: [0, R - 2]
-                    const int lx = (int)fx - (x0 - 1), ly = (int)fy - (y0 - 1), lz = (int)fz - (z0 - 1);
-                    if ((unsigned)lx > (unsigned)(RX - 2) || (unsigned)ly > (unsigned)(RY - 2) ||
-                        (unsigned)lz > (unsigned)(RZ - 2))
-                        continue;
+                    int lx = (int)fx - (x0 - 1), ly = (int)fy - (y0 - 1), lz = (int)fz - (z0 - 1);
+                    const bool inr = (unsigned)lx <= (unsigned)(RX - 2) && (unsigned)ly <= (unsigned)(RY - 2) &&
+                                     (unsigned)lz <= (unsigned)(RZ - 2);
+                    lx = min(max(lx, 0), RX - 2);
+                    ly = min(max(ly, 0), RY - 2);
+                    lz = min(max(lz, 0), RZ - 2);
+                    const float yk = inr ? ys : 0.f;
                     const float wx = x - fx, wy = yy - fy, wz = z - fz;
-                    const float c0 = ys * (1.f - wz), c1 = ys * wz;
+                    const float c0 = yk * (1.f - wz), c1 = yk * wz;
                     const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
                     const float ux = 1.f - wx;
                     if (F32) {

@@ -130,9 +130,10 @@ __device__ __forceinline__ float4 gather4(cudaTextureObject_t t, int layer, floa
 template <int MODE>
 __global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, float *__restrict__ proj,
                                                        const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
-                                                       int nvb, int b) {
+                                                       int nvb, int b0) {
     const int a = blockIdx.y;
-    const int vb = blockIdx.z;
+    const int vb = blockIdx.z % nvb, bl = blockIdx.z / nvb, b = b0 + bl;
+    const int lz0 = bl * g.nz;  // first layer of this volume in the array
     int iu, iv;
     pixel_of(iu, iv, vb);
     const bool valid = iu < g.nu && iv < g.nv;
@@ -145,16 +146,27 @@ __global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, 
     const int kw1 = __reduce_max_sync(0xffffffffu, k1);
     const int nz = g.nz;
     float acc = 0.f;
+    // The eight corners are fetched again only when the sample leaves the
+    // previous sample's cell: with steps of about half a voxel, consecutive
+    // samples often share it, and in a warp stepping in lockstep through k
+    // the crossings of the dominant axis happen at nearly the same step.
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    float cfx = -3.0e38f, cfy = 0.f, cfz = 0.f;
     for (int k = kw0; k <= kw1; ++k) {
         if (k < k0 || k > k1) continue;
         const float kf = (float)k;
         const float x = fmaf(kf, r.gx, r.sx), y = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
         const float fx = floorf(x), fy = floorf(y), fz = floorf(z);
         const float wx = x - fx, wy = y - fy, wz = z - fz;
-        const int iz = (int)fz;
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 lo = iz >= 0 ? gather4(tex, iz, fx + 1.f, fy + 1.f) : zero;
-        const float4 hi = iz + 1 < nz ? gather4(tex, iz + 1, fx + 1.f, fy + 1.f) : zero;
+        if (fx != cfx || fy != cfy || fz != cfz) {
+            const int iz = (int)fz;
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            lo = iz >= 0 ? gather4(tex, lz0 + iz, fx + 1.f, fy + 1.f) : zero;
+            hi = iz + 1 < nz ? gather4(tex, lz0 + iz + 1, fx + 1.f, fy + 1.f) : zero;
+            cfx = fx;
+            cfy = fy;
+            cfz = fz;
+        }
         const float l0 = fmaf(wx, lo.z - lo.w, lo.w), l1 = fmaf(wx, lo.y - lo.x, lo.x);
         const float h0 = fmaf(wx, hi.z - hi.w, hi.w), h1 = fmaf(wx, hi.y - hi.x, hi.x);
         const float c0 = fmaf(wy, l1 - l0, l0), c1 = fmaf(wy, h1 - h0, h0);
@@ -366,19 +378,29 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
     if ((long long)nvb * batch > 65535 || g.nA > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid(nub, g.nA, nvb * batch), block(256);
     if (method == TG_INTERP && texture_fits(g)) {
+        // The batch is stacked as layers of one array (volume b holds layers
+        // b nz .. b nz + nz - 1) and projected in one launch when the layer
+        // limit allows it, else in groups.
+        const int per = 2048 / g.nz;  // volumes per array
+        const int group = batch < per ? batch : per;
+        Grid gl = g;
+        gl.nz = g.nz * group;
         TexCache tc;
-        cudaError_t e = texture_for(g, s, tc);
+        cudaError_t e = texture_for(gl, s, tc);
         if (e != cudaSuccess) return e;
-        dim3 grid1(nub, g.nA, nvb);
         const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-        for (int b = 0; b < batch; ++b) {
-            e = copy_to_texture(tc, vol + (size_t)b * nvox, g, s);
+        for (int b0 = 0; b0 < batch; b0 += group) {
+            const int nb = batch - b0 < group ? batch - b0 : group;
+            Grid gc = g;
+            gc.nz = g.nz * nb;
+            e = copy_to_texture(tc, vol + (size_t)b0 * nvox, gc, s);
             if (e != cudaSuccess) return e;
+            dim3 grid1(nub, g.nA, nvb * nb);
             switch (mode) {
-                case FP_STORE: k_fp_interp_tex<FP_STORE><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
-                case FP_RESID_W: k_fp_interp_tex<FP_RESID_W><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
-                case FP_STORE_NORM: k_fp_interp_tex<FP_STORE_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
-                case FP_RESID_NORM: k_fp_interp_tex<FP_RESID_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b); break;
+                case FP_STORE: k_fp_interp_tex<FP_STORE><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_RESID_W: k_fp_interp_tex<FP_RESID_W><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_STORE_NORM: k_fp_interp_tex<FP_STORE_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_RESID_NORM: k_fp_interp_tex<FP_RESID_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
                 default: return cudaErrorInvalidValue;
             }
             count_launch();

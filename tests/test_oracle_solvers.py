@@ -119,3 +119,21 @@ def test_ossart_blocks_match_dense(problem):
 def test_subsets_ragged_tail():
     blocks = oracle.subsets(7, 3)
     assert [list(b) for b in blocks] == [[0, 1, 2], [3, 4, 5], [6]]
+
+
+def test_oracle_gradient_is_exact_central_difference():
+    """The loss ||A x - b||^2 is quadratic, so a central difference equals the
+    gradient 2 A^T (A x - b) up to rounding (pins the gradient used to judge
+    the differentiable projector)."""
+    g = inputs.circular_geometry((8, 7, 6), (1.0,) * 3, (12, 10), (1.0, 1.0), 5, 60.0, 100.0)
+    rng = np.random.default_rng(4)
+    x, b = rng.random(g.vol_shape), rng.random(g.proj_shape)
+    grad = 2 * oracle.backproject(g, oracle.forward(g, x, "interp") - b, "matched")
+    h = 1e-3
+    for j in rng.choice(x.size, 12, replace=False):
+        e = np.zeros(x.size)
+        e[j] = h
+        e = e.reshape(x.shape)
+        fp = np.sum((oracle.forward(g, x + e, "interp") - b) ** 2)
+        fm = np.sum((oracle.forward(g, x - e, "interp") - b) ** 2)
+        assert (fp - fm) / (2 * h) == pytest.approx(grad.reshape(-1)[j], rel=1e-6, abs=1e-9)
