@@ -94,7 +94,7 @@ constexpr int RX = BX + 2, RY = BY + 2, RZ = BZ + 2;  // with the one-voxel rim
 constexpr int PX = RX + 1;                            // row pitch (bank spreading)
 constexpr int PP = PX * RY + 9;                       // plane pitch
 constexpr int ACC_WORDS = PP * RZ;                    // one accumulator class
-constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4;       // bytes: two classes
+constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4 + 1536 * 32;  // bytes: two classes + ray list
 constexpr float FINE = 64.f;                          // scale ratio of the classes
 constexpr int MT = 512;                               // threads per CTA
 constexpr int OWN = BX * BY * BZ / MT;                // owned voxels per thread
@@ -105,6 +105,76 @@ static_assert(OWN == 32 && MT == 512 && BX == 32 && BY == 32, "owned-voxel map a
 
 __device__ __forceinline__ unsigned int fixq(float v) {  // round(v) for |v| < 2^22
     return (unsigned int)(__float_as_int(v + MAGIC) - MAGIC_BITS);
+}
+
+// A ray of the current angle with samples in the brick's region.
+struct alignas(16) RayRec {
+    float gx, gy, gz;  // index-space step per sample
+    float ys;          // y, scaled to its fixed-point class
+    int ka, kc;        // samples ka..kc lie in the region (and in the volume)
+    int cls;           // 1: coarse class, 0: fine class
+    int pad;
+};
+constexpr int RAYCAP = 1536;  // rays per shared-memory list (a chunk of candidates)
+static_assert(MATCHED_SMEM == 2 * ACC_WORDS * 4 + RAYCAP * (int)sizeof(RayRec), "shared-memory layout");
+
+// Sets up ray (iu, iv) against the region [lo, hi) and fills rec; false
+// when it has no sample there or carries y = 0 (it would add nothing).
+template <bool F32>
+__device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const float *pa, int iu, int iv, bool edge,
+                                           float lox, float loy, float loz, float hix, float hiy, float hiz,
+                                           float ybig, float scale, float scale_f, RayRec &rec) {
+    const float yraw = __ldg(pa + (size_t)iv * g.nu + iu);
+    if (yraw == 0.f) return false;
+    Ray r;
+    int kb0 = 0, kb1 = 0x7fffffff;
+    if (edge) {
+        if (!ray_setup_outlined(A, g, iu, iv, r)) return false;
+        kb0 = r.k0;
+        kb1 = r.k1;
+    } else {
+        // the forward kernel's FP32 arithmetic for the sample positions
+        const float fu = (float)iu, fv = (float)iv;
+        const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
+        const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
+        const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
+        const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float invL = rsqrtf(ss);
+        const float f = g.delta * invL;
+        r.sx = A.Sg[0];
+        r.sy = A.Sg[1];
+        r.sz = A.Sg[2];
+        r.gx = dx * f * g.idx;
+        r.gy = dy * f * g.idy;
+        r.gz = dz * f * g.idz;
+    }
+    float klo = (float)kb0, khi = (float)kb1;
+    const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
+    const float lo[3] = {lox, loy, loz}, hi[3] = {hix, hiy, hiz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (gv[ax] != 0.f) {
+            const float ia = 1.f / gv[ax];
+            const float ka = (lo[ax] - sv[ax]) * ia, kc = (hi[ax] - sv[ax]) * ia;
+            klo = fmaxf(klo, fminf(ka, kc));
+            khi = fminf(khi, fmaxf(ka, kc));
+        } else if (sv[ax] < lo[ax] || sv[ax] >= hi[ax]) {
+            return false;
+        }
+    }
+    if (!(khi >= klo)) return false;
+    const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
+    if (ka > kc) return false;
+    const bool big = fabsf(yraw) > ybig;
+    rec.gx = r.gx;
+    rec.gy = r.gy;
+    rec.gz = r.gz;
+    rec.ys = F32 ? yraw : yraw * (big ? scale : scale_f);
+    rec.ka = ka;
+    rec.kc = kc;
+    rec.cls = big ? 1 : 0;
+    rec.pad = 0;
+    return true;
 }
 
 // F32: accumulate with FP32 shared atomics instead (read-modify-write loops,
@@ -131,6 +201,8 @@ __global__ void __launch_bounds__(MT, 1)
     // a FINE times finer scale, so that a few large rays (e.g. the heavily
     // weighted corner rays of SIRT residuals) do not coarsen the others.
     unsigned int *acc_f = acc + ACC_WORDS;
+    RayRec *rays = reinterpret_cast<RayRec *>(acc + 2 * ACC_WORDS);
+    __shared__ int s_cnt[2];  // rays listed, rays handed out
     const float gmax = __uint_as_float(ep.absmax[b]);
     const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
     const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
@@ -170,67 +242,83 @@ __global__ void __launch_bounds__(MT, 1)
             const int v0 = max((int)ceilf(vmin - 1e-3f), 0), v1 = min((int)floorf(vmax + 1e-3f), g.nv - 1);
             if (u1 < u0 || v1 < v0) continue;
             const float *pa = pb + (size_t)a * g.nv * g.nu;
-            // warp tasks: 32 x 16 pixel tiles, each split in 16 phases of
-            // 8 x 4 rays spaced four pixels apart
+            // Candidate rays in a bank-friendly order: candidate c is slot
+            // c % 32 of an 8 x 4 pattern of pixels four apart, in one of 16
+            // phases of a 32 x 16 pixel tile.  They are handled in chunks of
+            // RAYCAP: phase A sets every candidate up and keeps, in a shared
+            // list, those with samples in the region; phase B lets each lane
+            // pull the next listed ray as soon as its current one ends, so
+            // the lanes stay busy although rays cross the region over very
+            // different lengths.
             const int ntu = (u1 - u0 + 32) >> 5, ntv = (v1 - v0 + 16) >> 4;
-            const int ntask = ntu * ntv * 16;
-            for (int task = warp; task < ntask; task += nwarp) {
-                const int ph = task & 15, tile = task >> 4;
-                const int iu = u0 + (tile % ntu) * 32 + (lane & 7) * 4 + (ph & 3);
-                const int iv = v0 + (tile / ntu) * 16 + (lane >> 3) * 4 + (ph >> 2);
-                if (iu > u1 || iv > v1) continue;
-                const float yraw = __ldg(pa + (size_t)iv * g.nu + iu);
-                const bool big = fabsf(yraw) > ybig;
-                const float ys = F32 ? yraw : yraw * (big ? scale : scale_f);
-                unsigned int *const accc = big ? acc : acc_f;
-                Ray r;
-                int kb0 = 0, kb1 = 0x7fffffff;
-                if (edge) {
-                    if (!ray_setup_outlined(A, g, iu, iv, r)) continue;
-                    kb0 = r.k0;
-                    kb1 = r.k1;
-                } else {
-                    // the forward kernel's FP32 arithmetic for the sample positions
-                    const float fu = (float)iu, fv = (float)iv;
-                    const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
-                    const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
-                    const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
-                    const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float invL = rsqrtf(ss);
-                    const float f = g.delta * invL;
-                    r.sx = A.Sg[0];
-                    r.sy = A.Sg[1];
-                    r.sz = A.Sg[2];
-                    r.gx = dx * f * g.idx;
-                    r.gy = dy * f * g.idy;
-                    r.gz = dz * f * g.idz;
+            const int ncand = ntu * ntv * 16 * 32;
+            for (int c0 = 0; c0 < ncand; c0 += RAYCAP) {
+                const int cend = min(c0 + RAYCAP, ncand);
+                if (tid == 0) {
+                    s_cnt[0] = 0;
+                    s_cnt[1] = 0;
                 }
-                // samples of this ray inside the region
-                float klo = (float)kb0, khi = (float)kb1;
-                const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
-                const float lo[3] = {lox, loy, loz}, hi[3] = {hix, hiy, hiz};
-                bool miss = false;
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    if (gv[ax] != 0.f) {
-                        const float ia = 1.f / gv[ax];
-                        const float ka = (lo[ax] - sv[ax]) * ia, kc = (hi[ax] - sv[ax]) * ia;
-                        klo = fmaxf(klo, fminf(ka, kc));
-                        khi = fminf(khi, fmaxf(ka, kc));
-                    } else if (sv[ax] < lo[ax] || sv[ax] >= hi[ax]) {
-                        miss = true;
+                __syncthreads();
+                for (int cb = c0 + warp * 32; cb < cend; cb += MT) {  // warp-uniform trips
+                    const int cand = cb + lane;
+                    bool keep = false;
+                    RayRec rec;
+                    if (cand < cend) {
+                        const int task = cand >> 5, slot = cand & 31;
+                        const int ph = task & 15, tile = task >> 4;
+                        const int iu = u0 + (tile % ntu) * 32 + (slot & 7) * 4 + (ph & 3);
+                        const int iv = v0 + (tile / ntu) * 16 + (slot >> 3) * 4 + (ph >> 2);
+                        if (iu <= u1 && iv <= v1)
+                            keep = region_ray<F32>(A, g, pa, iu, iv, edge, lox, loy, loz, hix, hiy, hiz, ybig,
+                                                   scale, scale_f, rec);
                     }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(&s_cnt[0], __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (keep) rays[base + __popc(m & ((1u << lane) - 1u))] = rec;
                 }
-                if (miss || !(khi >= klo)) continue;
-                const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
-                // Branch-free body, two samples per trip for instruction-level
-                // parallelism.  A sample whose cell falls outside the rimmed
-                // region (FP32 rounding at the region's edge; its weights on
-                // owned voxels are zero) is clamped into it and adds zeros.
-#pragma unroll 2
-                for (int k = ka; k <= kc; ++k) {
-                    const float kf = (float)k;
-                    const float x = fmaf(kf, r.gx, r.sx), yy = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
+                __syncthreads();
+                const int nr = s_cnt[0];
+                int k = 1, kc = 0;
+                float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f;
+                unsigned int *accc = acc;
+                bool live = true;
+                const float sx = A.Sg[0], sy = A.Sg[1], sz = A.Sg[2];
+                while (true) {
+                    const bool need = live && k > kc;
+                    const unsigned m = __ballot_sync(0xffffffffu, need);
+                    if (m) {
+                        const int lead = __ffs(m) - 1;
+                        int base = 0;
+                        if (lane == lead) base = atomicAdd(&s_cnt[1], __popc(m));
+                        base = __shfl_sync(0xffffffffu, base, lead);
+                        if (need) {
+                            const int idx = base + __popc(m & ((1u << lane) - 1u));
+                            if (idx < nr) {
+                                const RayRec rr = rays[idx];
+                                gx = rr.gx;
+                                gy = rr.gy;
+                                gz = rr.gz;
+                                ys = rr.ys;
+                                k = rr.ka;
+                                kc = rr.kc;
+                                accc = rr.cls ? acc : acc_f;
+                            } else {
+                                live = false;
+                            }
+                        }
+                    }
+                    if (!__any_sync(0xffffffffu, live)) break;
+                    if (!live) continue;
+                    {
+                        // One sample: the forward kernel's FP32 position, its
+                        // eight corner weights.  A sample whose cell falls
+                        // outside the rimmed region (FP32 rounding at the
+                        // region's edge; its weights on owned voxels are zero)
+                        // is clamped into it and adds zeros.
+                        const float kf = (float)k;
+                        const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
                     const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
                     // local corner indices in the rimmed region: [0, R - 2]
                     int lx = (int)fx - (x0 - 1), ly = (int)fy - (y0 - 1), lz = (int)fz - (z0 - 1);
@@ -265,7 +353,10 @@ __global__ void __launch_bounds__(MT, 1)
                         atomicAdd(c + PP + PX, fixq(b11 * ux));
                         atomicAdd(c + PP + PX + 1, fixq(b11 * wx));
                     }
+                    }
+                    ++k;
                 }
+                __syncthreads();  // the list is refilled by the next chunk
             }
         }
         // end of a fixed-point period: move the owned sums to FP32
