@@ -126,6 +126,14 @@ tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngl
 tg_status tg_backproject_noalloc(const tg_geometry *geo, const double *angles, int nAngles,
                                  const float *proj, float *vol, int method, int batch, void *stream);
 
+/* Data-fit gradient of Eq. 4: grad = A^T (A vol - proj) for `batch`
+ * volumes sharing the geometry (A = TG_INTERP, A^T = TG_MATCHED).  proj may
+ * be NULL (then grad = A^T A vol).  accumulate == 1 adds the result to grad
+ * instead of overwriting it.  Buffers may be host or device memory; takes
+ * one projection set per batch item of stream-ordered scratch. */
+tg_status tg_gradient(const tg_geometry *geo, const double *angles, int nAngles, const float *vol,
+                      const float *proj, float *grad, int accumulate, int batch, void *stream);
+
 /* FDK (Sec. 2.1, direct methods): cosine pre-weight |(P-S).n|/|P-S|, Ram-Lak
  * row filter sampled at du*DSO/DSD (linear convolution, no wrap-around),
  * TG_FDK_WEIGHT backprojection.  Assumes equally spaced angles over 2 pi.
@@ -158,6 +166,67 @@ tg_status tg_ossart(const tg_geometry *geo, const double *angles, int nAngles, c
  * recurrence residual ||r_k|| after each iteration. */
 tg_status tg_cgls(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
                   float *vol, int niter, double *resid_hist, void *stream);
+
+/* ---- Learned-gradient network (the data-driven use the paper's PyTorch
+ * operator wrappers are for, Sec. 2.8: a network that maps the iterate and
+ * the data-fit gradient A^T(Ax - b) to an update).
+ * Activations are BF16 (raw 16-bit words), channels last:
+ * [n][nz][ny][nx][channels]; weights are FP32 [27][cout][cin] with offset
+ * index (kz*3 + ky)*3 + kx, rounded to BF16 inside the kernels; products
+ * accumulate in FP32.  Supported (cin, cout): (16,32), (32,32), (32,8),
+ * (32,16), (8,32), (16,16).  All buffers are device memory; calls are
+ * asynchronous on `stream`.  Invalid sizes or channel pairs return
+ * TG_ERR_ARG before anything is launched. */
+
+/* y[v,o] = bias[o] + sum_{d in {-1,0,1}^3} sum_i x[v+d,i] w[d,o,i], zero
+ * padding at each volume's faces, optional ReLU; y is BF16, or FP32 when
+ * out_f32 != 0.  bias may be NULL.  n volumes of nz*ny*nx voxels each. */
+tg_status tg_conv3d_forward(const void *x, const float *w, const float *bias, void *y, int n, int nz, int ny,
+                            int nx, int cin, int cout, int relu, int out_f32, void *stream);
+
+/* tg_conv3d_forward over nvol volumes of different sizes, packed back to
+ * back in x and y (volume k starts after the voxels of volumes 0..k-1).
+ * dims: host array [nvol][3] = (nz, ny, nx) per volume.  One launch covers
+ * every volume (a per-volume tile table in the kernel's parameters) when
+ * nvol <= 64; larger counts are split into launches of 64. */
+tg_status tg_conv3d_forward_ragged(const void *x, const float *w, const float *bias, void *y,
+                                   const int32_t *dims, int nvol, int cin, int cout, int relu, int out_f32,
+                                   void *stream);
+
+/* Gradient in the input of tg_conv3d_forward (without its ReLU):
+ * gx[u,i] = sum_d sum_o gy[u-d,o] w[d,o,i]; gy has cout channels (BF16),
+ * gx gets cin (BF16).  Takes 27*cin*cout floats of stream-ordered scratch. */
+tg_status tg_conv3d_backward_data(const void *gy, const float *w, void *gx, int n, int nz, int ny, int nx,
+                                  int cin, int cout, void *stream);
+
+/* Gradient in the weights: dw[d,o,i] = sum_v x[v+d,i] gy[v,o] (FP32,
+ * overwritten). */
+tg_status tg_conv3d_backward_weight(const void *x, const void *gy, float *dw, int n, int nz, int ny, int nx,
+                                    int cin, int cout, void *stream);
+
+/* Gradient in the bias: db[o] = sum_v gy[v,o] (FP32, overwritten);
+ * cout in {8, 16, 32}. */
+tg_status tg_conv3d_backward_bias(const void *gy, float *db, size_t nvox, int cout, void *stream);
+
+/* out = g where act > 0, else 0 (BF16, count elements): the ReLU's backward.
+ * out may alias g. */
+tg_status tg_relu_backward(const void *g, const void *act, void *out, size_t count, void *stream);
+
+/* Network input: out[v] = (sx x[v], sg grad[v], 0, ...) as BF16 with
+ * `channels` (8 or 16) per voxel; grad may be NULL (then 0). */
+tg_status tg_lg_pack(const float *x, const float *grad, void *out, size_t nvox, int channels, float sx,
+                     float sg, void *stream);
+
+/* Channels 0 and 1 of a BF16 [nvox][channels] tensor to FP32:
+ * a[v] = sa in[v,0] (accumulate == 0) or a[v] += sa in[v,0] (accumulate ==
+ * 1); b[v] = sb in[v,1] (b may be NULL). */
+tg_status tg_lg_unpack(const void *in, int channels, float *a, float *b, size_t nvox, float sa, float sb,
+                       int accumulate, void *stream);
+
+/* Learned update: xnext[v] = x[v] + so net[v * net_channels] (FP32);
+ * xnext may alias x. */
+tg_status tg_lg_update(const float *x, const float *net, float *xnext, size_t nvox, int net_channels, float so,
+                       void *stream);
 
 /* Bytes of device scratch a call would take (op: 0 forward, 1 backproject,
  * 2 fdk, 3 sirt, 4 ossart, 5 cgls; blocksize only for ossart). */

@@ -20,6 +20,10 @@ follow:
 * ``sirt``, ``ossart`` -- Kaczmarz-type methods (Sec. 2.1) with the ordered
   subsets update (Sec. 2.2.2, Eq. 6).
 * ``cgls`` -- CGLS (Sec. 2.1, Krylov methods; Hestenes and Stiefel).
+* ``conv`` -- the 3x3x3 convolutions of the learned-gradient network and
+  their transposes (the learned use of the PyTorch wrappers, Sec. 2.8).
+* ``learned`` -- one learned-gradient step x + Gamma(x, A^T(Ax - b)) and its
+  gradient by the chain rule.
 """
 from __future__ import annotations
 

@@ -1,14 +1,14 @@
 """The projector pair as differentiable PyTorch operators (TIGRE v3, Sec. 2.8:
-PyTorch operator wrappers, P:359-381), device resident.
+PyTorch operator wrappers), device resident.
 
 ``project(x, geo)`` is A x (interpolated projector) and its backward is the
 matched backprojection A^T; ``backproject(y, geo)`` is A^T y with backward
 A.  Both run on libtg through the C ABI, on the caller's CUDA stream, for a
 single volume [nz, ny, nx] or a batch [B, nz, ny, nx] in one launch.  The
-paper's wrapper copies through NumPy on every call (P:383); here nothing
+paper's wrapper copies through NumPy on every call; here nothing
 leaves the GPU.
 
-``unrolled_gd`` is the gradient step of Eq. 4 (P:203-205),
+``unrolled_gd`` is the gradient step of Eq. 4,
 x_{k+1} = x_k - eta A^T (A x_k - b), unrolled for a fixed number of steps,
 with eta = 1 / ||A||^2 from a seeded power iteration and optional per-step
 activation checkpointing (each step's intermediate projections are

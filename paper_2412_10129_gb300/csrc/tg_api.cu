@@ -321,6 +321,41 @@ tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngl
     return c.finish();
 }
 
+tg_status tg_gradient(const tg_geometry *geo, const double *angles, int nAngles, const float *vol,
+                      const float *proj, float *grad, int accumulate, int batch, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (batch < 0 || (accumulate != 0 && accumulate != 1)) return TG_ERR_ARG;
+    if (batch == 0) return TG_OK;
+    if (!vol || !grad) return TG_ERR_ARG;
+    const size_t nvox = vol_count(geo) * batch, nray = proj_count(geo, nAngles) * batch;
+    Call c(stream);
+    View<float> gv = stage_in(c, grad, nvox, accumulate != 0);
+    if (nAngles == 0) {
+        if (c.ok() && !accumulate) c.ok(cudaMemsetAsync(gv.dev, 0, nvox * sizeof(float), c.s));
+        stage_out(c, gv);
+        return c.finish();
+    }
+    View<const float> v = stage_in(c, vol, nvox, true);
+    View<const float> b = stage_in(c, proj, proj ? nray : 0, true);
+    float *r = c.alloc<float>(nray);
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    unsigned int *amax = c.alloc<unsigned int>((size_t)batch);
+    if (!c.ok()) return c.finish();
+    const Grid g = call_grid(geo, angles, nAngles);
+    // r = A x (no data) or r = b - A x, so that A^T (A x - b) = sign * A^T r
+    FpEpilogue fe{};
+    fe.b = b.dev;
+    c.ok(launch_forward(TG_INTERP, g, dA, v.dev, r, batch, b.dev ? FP_RESID_W : FP_STORE, fe, c.s));
+    BpEpilogue e{};
+    e.scale = b.dev ? -g.delta : g.delta;
+    e.lambda = 1.f;
+    e.absmax = amax;
+    if (c.ok()) c.ok(launch_backproject(TG_MATCHED, g, dA, r, gv.dev, batch, accumulate ? BP_SIRT : BP_STORE, e, c.s));
+    stage_out(c, gv);
+    return c.finish();
+}
+
 tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
                  int filter, void *stream) {
     tg_status st = check_common(geo, angles, nAngles);

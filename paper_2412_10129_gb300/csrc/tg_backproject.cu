@@ -58,7 +58,7 @@ __device__ __forceinline__ void bp_epilogue(float sum, bool valid, size_t vidx, 
         if (valid) vol[vidx] = ep.scale * sum;
     } else if (MODE == BP_SIRT) {
         if (valid) {
-            float x = fmaf(ep.lambda * ep.Vw[widx], ep.scale * sum, vol[vidx]);
+            float x = fmaf(ep.lambda * (ep.Vw ? ep.Vw[widx] : 1.f), ep.scale * sum, vol[vidx]);
             if (ep.nonneg) x = fmaxf(x, 0.f);
             vol[vidx] = x;
         }

@@ -48,7 +48,7 @@ __device__ __forceinline__ void fp_epilogue(float sum, bool valid, size_t pidx, 
     if (MODE == FP_STORE) {
         if (valid) proj[pidx] = sum;
     } else if (MODE == FP_RESID_W) {
-        if (valid) proj[pidx] = ep.W[widx] * (ep.b[pidx] - sum);
+        if (valid) proj[pidx] = (ep.W ? ep.W[widx] : 1.f) * (ep.b[pidx] - sum);
     } else if (MODE == FP_STORE_NORM) {
         if (valid) proj[pidx] = sum;
         const double d = valid ? (double)sum : 0.0;

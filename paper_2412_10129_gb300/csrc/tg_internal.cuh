@@ -72,12 +72,12 @@ enum BpMode {
 
 struct FpEpilogue {
     const float *b;      // measured data (FP_RESID_*), same layout as proj
-    const float *W;      // per-ray weight (FP_RESID_W), [nA][nv][nu], shared across batch
+    const float *W;      // per-ray weight (FP_RESID_W), [nA][nv][nu], shared across batch; null = 1
     double *norm;        // FP64 accumulator (one per batch item)
 };
 
 struct BpEpilogue {
-    const float *Vw;     // per-voxel weight (BP_SIRT), [nz][ny][nx]
+    const float *Vw;     // per-voxel weight (BP_SIRT), [nz][ny][nx]; null = 1
     float lambda;
     int nonneg;
     float scale;         // BP_STORE multiplier
@@ -106,6 +106,23 @@ cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsig
                          cudaStream_t s);
 cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const float *proj, float *out,
                               int batch, cudaStream_t s);
+
+// Learned-gradient network kernels (tg_conv.cu).
+cudaError_t launch_conv3d(const void *x, const float *w, const float *bias, void *y, int N, int Z, int Y, int X,
+                          int cin, int cout, int relu, int out_f32, cudaStream_t s);
+cudaError_t launch_conv3d_ragged(const void *x, const float *w, const float *bias, void *y, const int *dims,
+                                 int nvol, int cin, int cout, int relu, int out_f32, cudaStream_t s);
+cudaError_t launch_conv3d_wgrad(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, int cin,
+                                int cout, cudaStream_t s);
+cudaError_t launch_flip_weights(const float *w, float *wb, int cin, int cout, cudaStream_t s);
+cudaError_t launch_bias_grad(const void *gy, float *db, size_t nvox, int cout, cudaStream_t s);
+cudaError_t launch_relu_backward(const void *g, const void *act, void *out, size_t n, cudaStream_t s);
+cudaError_t launch_lg_pack(const float *a, const float *b, void *out, size_t nvox, int C, float sa, float sb,
+                           cudaStream_t s);
+cudaError_t launch_lg_unpack(const void *in, int C, float *a, float *b, size_t nvox, float sa, float sb, int accumulate,
+                             cudaStream_t s);
+cudaError_t launch_lg_update(const float *x, const float *net, float *xn, size_t nvox, int stride, float so,
+                             cudaStream_t s);
 
 // Vector kernels (tg_vector.cu).
 cudaError_t launch_safe_inverse(float *a, size_t n, cudaStream_t s);

@@ -145,9 +145,13 @@ def config_autograd() -> Geometry:
     return circular_geometry((128, 128, 128), (1.0,) * 3, (192, 192), (1.2, 1.2), 180, 1000.0, 1536.0)
 
 
-def config_learned(n: int = 256) -> Geometry:
-    """n^3 at 1 mm, 60 angles, 512^2 detector at 0.8 mm."""
-    return circular_geometry((n, n, n), (1.0,) * 3, (512, 512), (0.8, 0.8), 60, 1000.0, 1536.0)
+def config_learned(n: int = 256, n_angles: int = 60) -> Geometry:
+    """Sparse-view learned-reconstruction workload: a 256 mm cube as n^3
+    voxels (1 mm at n = 256), 60 angles over 2 pi, a (2n)^2 detector whose
+    pixels (0.8 mm at n = 256) scale with the voxels, so that smaller n is the
+    same scan at a coarser grid."""
+    s = 256.0 / n
+    return circular_geometry((n, n, n), (s,) * 3, (2 * n, 2 * n), (0.8 * s, 0.8 * s), n_angles, 1000.0, 1536.0)
 
 
 # ---------------------------------------------------------------------------
@@ -231,6 +235,15 @@ def voxelize_ellipsoids(geo: Geometry, ell: np.ndarray, dtype=np.float32) -> np.
 
 def ellipsoid_phantom(geo: Geometry, n: int, seed: int, **kw) -> np.ndarray:
     return voxelize_ellipsoids(geo, random_ellipsoids(geo, n, seed, **kw))
+
+
+def learned_phantom(geo: Geometry, seed: int, n: int = 20) -> np.ndarray:
+    """Phantom of the learned-reconstruction workload: n ellipsoids with
+    semi-axes 5-30 % of R (large enough to stay several voxels wide on the
+    coarse training grids), otherwise the recipe above."""
+    ext = np.asarray(geo.nVoxel, float) * np.asarray(geo.dVoxel, float)
+    R = 0.5 * min(ext[0], ext[1])
+    return voxelize_ellipsoids(geo, random_ellipsoids(geo, n, seed, semi_axes=(0.05 * R, 0.3 * R)))
 
 
 def porous_cylinder(geo: Geometry, seed: int, n_pores: int = 500, mu: float = 0.03) -> np.ndarray:

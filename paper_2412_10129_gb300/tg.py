@@ -74,6 +74,18 @@ def load():
                                   ctypes.POINTER(ctypes.c_size_t)],
             "tg_count_samples": [G, _DP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _VP],
             "tg_backproject_noalloc": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
+            "tg_gradient": [G, _DP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
+            "tg_conv3d_forward": [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 8 + [_VP],
+            "tg_conv3d_forward_ragged": [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int32)] + [ctypes.c_int] * 5
+                                        + [_VP],
+            "tg_conv3d_backward_data": [_VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP],
+            "tg_conv3d_backward_weight": [_VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP],
+            "tg_conv3d_backward_bias": [_VP, _VP, ctypes.c_size_t, ctypes.c_int, _VP],
+            "tg_relu_backward": [_VP, _VP, _VP, ctypes.c_size_t, _VP],
+            "tg_lg_pack": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_float, ctypes.c_float, _VP],
+            "tg_lg_unpack": [_VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_int, _VP],
+            "tg_lg_update": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_float, _VP],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -204,6 +216,20 @@ def backproject_noalloc(geo, proj, method: str = "matched", out=None, stream=Non
     return out
 
 
+def gradient(geo, vol, proj=None, out=None, accumulate: bool = False, stream=None):
+    """A^T (A x - b) (Eq. 4's data-fit gradient; b = 0 when ``proj`` is None):
+    vol [(B,) nz, ny, nx] -> [(B,) nz, ny, nx]; ``accumulate`` adds into ``out``."""
+    G = _Geo(geo)
+    B, batched = _batch(vol, 3)
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs out")
+        out = _empty_like_kind(vol, vol.shape)
+    _check("tg_gradient", load().tg_gradient(G.ref, G.ang, G.n, _ptr(vol), None if proj is None else _ptr(proj),
+                                             _ptr(out), int(bool(accumulate)), B, _stream(vol, stream)))
+    return out
+
+
 def fdk(geo, proj, out=None, stream=None):
     """FDK reconstruction (Ram-Lak)."""
     G = _Geo(geo)
@@ -298,3 +324,132 @@ def status_string(code: int) -> str:
 def _sync(t):
     if not isinstance(t, np.ndarray) and t.is_cuda:
         _torch().cuda.current_stream(t.device).synchronize()
+
+
+# ---------------------------------------------------------------------------
+# Learned-gradient network kernels: activations are bfloat16 CUDA tensors,
+# channels last [n, nz, ny, nx, c]; weights float32 [27, cout, cin].
+# ---------------------------------------------------------------------------
+
+def _dptr(t, dtype):
+    """Data pointer of a contiguous CUDA tensor of the given torch dtype."""
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype}")
+    return t.data_ptr()
+
+
+def _cs(t, stream):
+    return _stream(t, stream)
+
+
+def conv3d(x, w, bias=None, relu: bool = False, out_f32: bool = False, out=None, stream=None):
+    """tg_conv3d_forward: x [n, nz, ny, nx, cin] bf16 -> [n, nz, ny, nx, cout]."""
+    torch = _torch()
+    n, nz, ny, nx, cin = x.shape
+    cout = int(w.shape[1])
+    if tuple(w.shape) != (27, cout, cin):
+        raise ValueError("weights must be [27, cout, cin]")
+    if out is None:
+        out = torch.empty((n, nz, ny, nx, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device=x.device)
+    _check("tg_conv3d_forward", load().tg_conv3d_forward(
+        _dptr(x, torch.bfloat16), _dptr(w, torch.float32), None if bias is None else _dptr(bias, torch.float32),
+        _dptr(out, torch.float32 if out_f32 else torch.bfloat16), n, nz, ny, nx, cin, cout, int(bool(relu)),
+        int(bool(out_f32)), _cs(x, stream)))
+    return out
+
+
+def conv3d_ragged(x, dims, w, bias=None, relu: bool = False, out_f32: bool = False, out=None, stream=None):
+    """tg_conv3d_forward_ragged: volumes of sizes ``dims`` [(nz, ny, nx), ...]
+    packed back to back in x [sum voxels, cin] (bf16) -> [sum voxels, cout]."""
+    torch = _torch()
+    cout, cin = int(w.shape[1]), int(w.shape[2])
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(-1, 3))
+    nvox = int(np.sum(np.prod(d.astype(np.int64), axis=1)))
+    if x.numel() != nvox * cin:
+        raise ValueError("x does not hold the voxels of dims")
+    if out is None:
+        out = torch.empty((nvox, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device=x.device)
+    _check("tg_conv3d_forward_ragged", load().tg_conv3d_forward_ragged(
+        _dptr(x, torch.bfloat16), _dptr(w, torch.float32), None if bias is None else _dptr(bias, torch.float32),
+        _dptr(out, torch.float32 if out_f32 else torch.bfloat16), d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        int(d.shape[0]), cin, cout, int(bool(relu)), int(bool(out_f32)), _cs(x, stream)))
+    return out
+
+
+def conv3d_backward_data(gy, w, out=None, stream=None):
+    """tg_conv3d_backward_data: gy [n, nz, ny, nx, cout] bf16 -> gx [.., cin] bf16."""
+    torch = _torch()
+    n, nz, ny, nx, cout = gy.shape
+    cin = int(w.shape[2])
+    if out is None:
+        out = torch.empty((n, nz, ny, nx, cin), dtype=torch.bfloat16, device=gy.device)
+    _check("tg_conv3d_backward_data", load().tg_conv3d_backward_data(
+        _dptr(gy, torch.bfloat16), _dptr(w, torch.float32), _dptr(out, torch.bfloat16), n, nz, ny, nx, cin, cout,
+        _cs(gy, stream)))
+    return out
+
+
+def conv3d_backward_weight(x, gy, out=None, stream=None):
+    """tg_conv3d_backward_weight: dw [27, cout, cin] float32."""
+    torch = _torch()
+    n, nz, ny, nx, cin = x.shape
+    cout = int(gy.shape[4])
+    if out is None:
+        out = torch.empty((27, cout, cin), dtype=torch.float32, device=x.device)
+    _check("tg_conv3d_backward_weight", load().tg_conv3d_backward_weight(
+        _dptr(x, torch.bfloat16), _dptr(gy, torch.bfloat16), _dptr(out, torch.float32), n, nz, ny, nx, cin, cout,
+        _cs(x, stream)))
+    return out
+
+
+def conv3d_backward_bias(gy, out=None, stream=None):
+    """tg_conv3d_backward_bias: db [cout] float32."""
+    torch = _torch()
+    cout = int(gy.shape[-1])
+    if out is None:
+        out = torch.empty((cout,), dtype=torch.float32, device=gy.device)
+    _check("tg_conv3d_backward_bias", load().tg_conv3d_backward_bias(
+        _dptr(gy, torch.bfloat16), _dptr(out, torch.float32), gy.numel() // cout, cout, _cs(gy, stream)))
+    return out
+
+
+def relu_backward(g, act, out=None, stream=None):
+    """tg_relu_backward (bf16); ``out`` may be ``g``."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(g)
+    _check("tg_relu_backward", load().tg_relu_backward(
+        _dptr(g, torch.bfloat16), _dptr(act, torch.bfloat16), _dptr(out, torch.bfloat16), g.numel(), _cs(g, stream)))
+    return out
+
+
+def lg_pack(x, grad, channels: int, sx: float = 1.0, sg: float = 1.0, out=None, stream=None):
+    """tg_lg_pack: FP32 volume(s) -> bf16 [..., channels] = (sx x, sg grad, 0, ...)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(tuple(x.shape) + (channels,), dtype=torch.bfloat16, device=x.device)
+    _check("tg_lg_pack", load().tg_lg_pack(
+        _dptr(x, torch.float32), None if grad is None else _dptr(grad, torch.float32), _dptr(out, torch.bfloat16),
+        x.numel(), int(channels), float(sx), float(sg), _cs(x, stream)))
+    return out
+
+
+def lg_unpack(t, a, b=None, sa: float = 1.0, sb: float = 1.0, accumulate: bool = False, stream=None):
+    """tg_lg_unpack: a (=|+=) sa t[..., 0]; b = sb t[..., 1]."""
+    torch = _torch()
+    _check("tg_lg_unpack", load().tg_lg_unpack(
+        _dptr(t, torch.bfloat16), int(t.shape[-1]), _dptr(a, torch.float32),
+        None if b is None else _dptr(b, torch.float32), a.numel(), float(sa), float(sb), int(bool(accumulate)),
+        _cs(t, stream)))
+    return a
+
+
+def lg_update(x, net, so: float = 1.0, out=None, stream=None):
+    """tg_lg_update: x + so net[..., 0] (FP32); ``out`` may be ``x``."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(x)
+    _check("tg_lg_update", load().tg_lg_update(
+        _dptr(x, torch.float32), _dptr(net, torch.float32), _dptr(out, torch.float32), x.numel(), int(net.shape[-1]),
+        float(so), _cs(x, stream)))
+    return out

@@ -1,0 +1,295 @@
+"""The learned-gradient network's kernels and its unrolled scheme on the GPU.
+
+Convolutions are checked against the FP64 oracle (oracle.conv) on
+BF16-representable inputs and BF16-rounded weights, so the only differences
+left are FP32 accumulation order (FP32 outputs: 1e-5 relative L2) and the
+final rounding of BF16 outputs (half a BF16 ulp, 2^-9 relative, plus the
+accumulation error).  The data-fit gradient A^T(Ax - b) is checked against
+the oracle's projector pair (2e-5 relative L2: one forward and one
+backprojection, 1e-5 each).  A whole learned step and its gradient are
+checked against oracle.learned; the network's activations are BF16 there
+(the oracle mirrors the forward rounding), so the bound is 1e-2 relative L2
+(ten BF16 roundings of about 2^-9 each along the chain, with margin).
+Training reduces the loss and beats the untrained scheme on held-out
+phantoms; batched and ragged (uneven-size) inference reproduce the
+one-volume results bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import max_rel, rel_l2
+from oracle import conv as oconv
+from oracle import learned as olearned
+from paper_2412_10129_gb300 import inputs, tg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PAIRS = [(16, 32), (32, 32), (32, 8), (32, 16), (8, 32), (16, 16)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2412_10129_gb300 import build
+    build.build()
+    tg.load()
+
+
+def lm():
+    from paper_2412_10129_gb300 import learned
+    return learned
+
+
+def bf16_input(rng, shape, scale=1.0):
+    """Random values that BF16 represents exactly, as (torch bf16 CUDA, float64 numpy)."""
+    a = oconv.bf16_round((rng.standard_normal(shape) * scale).astype(np.float32))
+    return torch.from_numpy(a).to(torch.bfloat16).cuda(), a.astype(np.float64)
+
+
+def to_oracle_w(w):
+    """[27, cout, cin] kernel layout -> oracle W[kz, ky, kx, cin, cout]."""
+    w = np.asarray(w, np.float64)
+    return w.reshape(3, 3, 3, w.shape[1], w.shape[2]).transpose(0, 1, 2, 4, 3)
+
+
+def rand_w(rng, cin, cout):
+    w = (rng.standard_normal((27, cout, cin)) * np.sqrt(2.0 / (27 * cin))).astype(np.float32)
+    return torch.from_numpy(w).cuda(), to_oracle_w(oconv.bf16_round(w))
+
+
+def check_bf16_out(y, ref):
+    y = y.float().cpu().numpy().astype(np.float64)
+    m = np.abs(ref).max()
+    assert np.all(np.abs(y - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * m)
+
+
+@pytest.mark.parametrize("cin,cout", PAIRS)
+@pytest.mark.parametrize("shape", [(2, 5, 6, 37), (1, 3, 4, 130)])
+def test_conv_forward_matches_oracle(cin, cout, shape):
+    rng = np.random.default_rng(cin * 100 + cout + shape[3])
+    x, xo = bf16_input(rng, shape + (cin,))
+    w, wo = rand_w(rng, cin, cout)
+    bias = rng.standard_normal(cout).astype(np.float32) * 0.1
+    bt = torch.from_numpy(bias).cuda()
+    for relu in (False, True):
+        ref = oconv.conv3d(xo, wo, bias, relu=relu)
+        y = tg.conv3d(x, w, bt, relu=relu, out_f32=True).cpu().numpy()
+        assert rel_l2(y, ref) <= 1e-5
+        assert max_rel(y, ref) <= 1e-4
+        check_bf16_out(tg.conv3d(x, w, bt, relu=relu), ref)
+    y = tg.conv3d(x, w, None, out_f32=True).cpu().numpy()
+    assert rel_l2(y, oconv.conv3d(xo, wo)) <= 1e-5
+
+
+def test_conv_single_voxel_and_thin_volumes():
+    rng = np.random.default_rng(5)
+    for shape in [(1, 1, 1, 1), (1, 1, 1, 129), (3, 2, 1, 3), (1, 1, 9, 1)]:
+        x, xo = bf16_input(rng, shape + (32,))
+        w, wo = rand_w(rng, 32, 32)
+        y = tg.conv3d(x, w, None, out_f32=True).cpu().numpy()
+        assert rel_l2(y, oconv.conv3d(xo, wo)) <= 1e-5
+
+
+def test_ragged_conv_matches_per_volume_and_oracle():
+    rng = np.random.default_rng(7)
+    dims = [(4, 5, 130), (3, 7, 20), (6, 2, 129), (1, 1, 1)]
+    xs = [bf16_input(rng, (1,) + d + (32,)) for d in dims]
+    w, wo = rand_w(rng, 32, 16)
+    bias = torch.from_numpy(rng.standard_normal(16).astype(np.float32)).cuda()
+    packed = torch.cat([x.reshape(-1, 32) for x, _ in xs]).contiguous()
+    for out_f32 in (False, True):
+        y = tg.conv3d_ragged(packed, dims, w, bias, relu=True, out_f32=out_f32)
+        off = 0
+        for (x, xo), d in zip(xs, dims):
+            n = int(np.prod(d))
+            one = tg.conv3d(x, w, bias, relu=True, out_f32=out_f32).reshape(-1, 16)
+            assert torch.equal(y[off:off + n], one)
+            ref = oconv.conv3d(xo, wo, bias.cpu().numpy(), relu=True).reshape(-1, 16)
+            if out_f32:
+                assert rel_l2(y[off:off + n].cpu().numpy(), ref) <= 1e-5
+            else:
+                check_bf16_out(y[off:off + n], ref)
+            off += n
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 8)])
+def test_conv_backward_data_matches_oracle(cin, cout):
+    rng = np.random.default_rng(11 + cin + cout)
+    gy, gyo = bf16_input(rng, (2, 4, 5, 131, cout))
+    w, wo = rand_w(rng, cin, cout)
+    gx = tg.conv3d_backward_data(gy, w)
+    check_bf16_out(gx, oconv.conv3d_backward_data(gyo, wo))
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 8)])
+def test_conv_backward_weight_and_bias_match_oracle(cin, cout):
+    rng = np.random.default_rng(13 + cin + cout)
+    x, xo = bf16_input(rng, (2, 5, 6, 70, cin))
+    gy, gyo = bf16_input(rng, (2, 5, 6, 70, cout))
+    dw = tg.conv3d_backward_weight(x, gy).cpu().numpy()
+    ref = oconv.conv3d_backward_weight(xo, gyo)            # [3,3,3,cin,cout]
+    assert rel_l2(to_oracle_w(dw), ref) <= 1e-5
+    db = tg.conv3d_backward_bias(gy).cpu().numpy()
+    assert rel_l2(db, gyo.sum(axis=(0, 1, 2, 3))) <= 1e-5
+
+
+def test_elementwise_kernels():
+    rng = np.random.default_rng(17)
+    g, go = bf16_input(rng, (3, 4, 5, 32))
+    a, ao = bf16_input(rng, (3, 4, 5, 32))
+    out = tg.relu_backward(g, a).float().cpu().numpy()
+    np.testing.assert_array_equal(out, np.where(ao > 0, go, 0.0))
+    tg.relu_backward(g, a, out=g)                       # in place
+    np.testing.assert_array_equal(g.float().cpu().numpy(), out)
+
+    x = torch.from_numpy(rng.random((2, 3, 4, 5)).astype(np.float32)).cuda()
+    gr = torch.from_numpy(rng.standard_normal((2, 3, 4, 5)).astype(np.float32)).cuda()
+    for C in (8, 16):
+        p = tg.lg_pack(x, gr, C, 3.0, -0.5).float().cpu().numpy()
+        np.testing.assert_array_equal(p[..., 0], oconv.bf16_round(3.0 * x.cpu().numpy()))
+        np.testing.assert_array_equal(p[..., 1], oconv.bf16_round(np.float32(-0.5) * gr.cpu().numpy()))
+        assert not np.any(p[..., 2:])
+        p0 = tg.lg_pack(x, None, C).float().cpu().numpy()
+        assert not np.any(p0[..., 1:])
+    t = tg.lg_pack(x, gr, 16, 1.0, 1.0)
+    a = torch.full_like(x, 2.0)
+    b = torch.empty_like(x)
+    tg.lg_unpack(t, a, b, 2.0, 4.0, accumulate=True)
+    tf = t.float()
+    torch.testing.assert_close(a, 2.0 + 2.0 * tf[..., 0], rtol=0, atol=0)
+    torch.testing.assert_close(b, 4.0 * tf[..., 1], rtol=0, atol=0)
+    net = torch.from_numpy(rng.standard_normal((2, 3, 4, 5, 8)).astype(np.float32)).cuda()
+    xn = tg.lg_update(x, net, 0.25)
+    torch.testing.assert_close(xn, x + 0.25 * net[..., 0], rtol=1e-7, atol=0)
+
+
+def test_data_gradient_matches_oracle():
+    g = inputs.random_geometry((40, 36, 28), (1.0, 1.1, 0.9), (64, 48), (1.3, 1.2), 12, seed=3)
+    rng = np.random.default_rng(19)
+    x = rng.random((2,) + g.vol_shape).astype(np.float32)
+    b = rng.random((2,) + g.proj_shape).astype(np.float32)
+    xt, bt = torch.from_numpy(x).cuda(), torch.from_numpy(b).cuda()
+    gr = tg.gradient(g, xt, bt).cpu().numpy()
+    for k in range(2):
+        ref = oracle.backproject(g, oracle.forward(g, x[k]) - b[k])
+        assert rel_l2(gr[k], ref) <= 2e-5
+    nb = tg.gradient(g, xt[0], None).cpu().numpy()
+    ref0 = oracle.backproject(g, oracle.forward(g, x[0]))
+    assert rel_l2(nb, ref0) <= 2e-5
+    acc = torch.full_like(xt[0], 1.5)
+    tg.gradient(g, xt[0], None, out=acc, accumulate=True)
+    assert rel_l2(acc.cpu().numpy(), ref0 + 1.5) <= 2e-5
+    # host buffers take the same path through staging
+    assert rel_l2(tg.gradient(g, x[1], b[1]), oracle.backproject(g, oracle.forward(g, x[1]) - b[1])) <= 2e-5
+
+
+def _small_problem(seed=0, n=24):
+    g = inputs.circular_geometry((n, n, n), (4.0,) * 3, (2 * n, 2 * n), (3.2, 3.2), 15, 1000.0, 1536.0)
+    L = lm()
+    b, x0, gt = L.make_sample(g, seed, I0=1e4)
+    return g, b, x0, gt
+
+
+def test_learned_step_matches_oracle():
+    L = lm()
+    g, b, x0, gt = _small_problem(seed=3)
+    net = L.LearnedGradient(seed=1, init_scale=1.0).cuda()
+    with torch.no_grad():                 # make every weight matter
+        net.weights[-1].add_(0.05 * torch.randn(net.weights[-1].shape, generator=torch.Generator().manual_seed(2))
+                             .cuda())
+        net.weights[-1][:, 1:, :] = 0.0
+    eta = 1.0 / lm().operator_norm_sq(g)
+    sx = 1.0 / L.MU_REF
+    x = x0.clone().requires_grad_(True)
+    xn = net.step(x[None], b[None], g, eta)[0]
+    gbar = torch.from_numpy(np.random.default_rng(4).standard_normal(g.vol_shape).astype(np.float32)).cuda()
+    torch.sum(xn * gbar).backward()
+    Ws = [to_oracle_w(oconv.bf16_round(w.detach().cpu().numpy())) for w in net.weights]
+    Bs = [c.detach().cpu().numpy().astype(np.float64) for c in net.biases]
+    xo = x0.cpu().numpy().astype(np.float64)
+    bo = b.cpu().numpy().astype(np.float64)
+    ref, _ = olearned.step(g, xo, bo, Ws, Bs, sx, sx * eta, 1.0 / sx, round_act=oconv.bf16_round)
+    upd = xn.detach().cpu().numpy() - xo
+    assert rel_l2(upd, ref - xo) <= 1e-2
+    gx, dWs, dBs = olearned.step_backward(g, xo, bo, Ws, Bs, sx, sx * eta, 1.0 / sx, gbar.cpu().numpy())
+    assert rel_l2(x.grad.cpu().numpy() - gbar.cpu().numpy(), gx - gbar.cpu().numpy()) <= 1e-2
+    for li in range(5):
+        dw = to_oracle_w(net.weights[li].grad.cpu().numpy())
+        if li == 0:
+            dw, rw = dw[:, :, :, :2], dWs[li][:, :, :, :2]   # padded input channels carry zeros
+        else:
+            rw = dWs[li]
+        if li == 4:
+            dw, rw = dw[..., :1], rw[..., :1]                 # padded output channels are unused
+        assert rel_l2(dw, rw) <= 1e-2, li
+        db = net.biases[li].grad.cpu().numpy()
+        if li == 4:
+            db, dBs[li] = db[:1], dBs[li][:1]
+        assert rel_l2(db, dBs[li]) <= 1e-2, li
+
+
+def test_gd_init_is_gradient_descent():
+    """With its initial weights the network is one gradient step of Eq. 4:
+    x - eta A^T(Ax - b), up to the BF16 rounding of the gradient channel."""
+    L = lm()
+    g, b, x0, gt = _small_problem(seed=5)
+    net = L.LearnedGradient(seed=0).cuda()
+    eta = 1.0 / lm().operator_norm_sq(g)
+    with torch.no_grad():
+        xn = net.step(x0[None], b[None], g, eta)[0]
+        gd = x0 - eta * tg.gradient(g, x0, b)
+    assert rel_l2((xn - x0).cpu().numpy(), (gd - x0).cpu().numpy()) <= 2.0 ** -7
+
+
+def test_batched_and_ragged_inference_match_single():
+    L = lm()
+    net = L.LearnedGradient(seed=3, init_scale=1.0).cuda()
+    with torch.no_grad():
+        net.weights[-1].add_(0.02)
+        net.weights[-1][:, 1:, :] = 0.0
+    probs = []
+    for k, n in enumerate((16, 24, 20)):
+        g = inputs.circular_geometry((n, n + 2, n - 3), (4.0,) * 3, (2 * n, 2 * n), (3.2, 3.2), 12, 1000.0, 1536.0)
+        b, x0, gt = L.make_sample(g, 40 + k)
+        probs.append((g, b, x0, 1.0 / lm().operator_norm_sq(g)))
+    with torch.no_grad():
+        singles = [net(x0, b, g, steps=3, eta=eta) for g, b, x0, eta in probs]
+        rag = L.infer_ragged(net, [p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs], steps=3,
+                             etas=[p[3] for p in probs])
+        for s, r in zip(singles, rag):
+            assert torch.equal(s, r)
+        g, b, x0, eta = probs[0]
+        b2 = torch.stack([b, b.flip(0)])
+        x02 = torch.stack([x0, x0.flip(0)])
+        both = net(x02, b2, g, steps=3, eta=eta)
+        assert torch.equal(both[0], singles[0])
+        assert torch.equal(both[1], net(x02[1], b2[1], g, steps=3, eta=eta))
+
+
+def test_training_improves_on_the_untrained_scheme():
+    """A short training run (32^3 at 8 mm, 15 angles, 48 phantoms) lowers the
+    loss, and the trained scheme beats the untrained one (plain gradient
+    descent) on held-out phantoms, judged by PSNR and by the oracle's FP64
+    data residual staying of the same order."""
+    L = lm()
+    g = inputs.circular_geometry((32,) * 3, (8.0,) * 3, (64, 64), (6.4, 6.4), 15, 1000.0, 1536.0)
+    torch.manual_seed(0)
+    net = L.LearnedGradient(seed=0).cuda()
+    eta = 1.0 / lm().operator_norm_sq(g)
+    test = [L.make_sample(g, 5000 + k) for k in range(3)]
+
+    def score():
+        with torch.no_grad():
+            return np.mean([L.psnr(net(x0, b, g, steps=5, eta=eta), gt) for b, x0, gt in test])
+
+    before = score()
+    losses = L.train(net, g, range(1000, 1048), steps=5, batch=2, lr=2e-3, epochs=2)
+    after = score()
+    assert np.mean(losses[-6:]) < 0.9 * np.mean(losses[:6])
+    assert after > before + 0.5
+    b, x0, gt = test[0]
+    with torch.no_grad():
+        x = net(x0, b, g, steps=5, eta=eta)
+    res = np.linalg.norm(oracle.forward(g, x.cpu().numpy()) - b.cpu().numpy().astype(np.float64))
+    res0 = np.linalg.norm(oracle.forward(g, x0.cpu().numpy()) - b.cpu().numpy().astype(np.float64))
+    assert np.isfinite(res) and res < 2.0 * res0
