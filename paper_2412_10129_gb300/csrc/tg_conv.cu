@@ -33,6 +33,14 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// m16n8k8: A (g, 2t..2t+1) and (g + 8, 2t..2t+1); B (k = 2t..2t+1, n = g)
+__device__ __forceinline__ void mma_bf16_k8(float (&d)[4], unsigned a0, unsigned a1, unsigned b0) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
 constexpr int CT = 128;   // output voxels (along x) per work item: 4 warps x 32
 constexpr int MAXV = 64;  // volumes per launch
 
@@ -52,6 +60,7 @@ template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(128) k_conv3d(const bf16 *__restrict__ x, const float *__restrict__ wt,
                                                 const float *__restrict__ bias, void *__restrict__ y,
                                                 const ConvTable tab) {
+    static_assert(CIN % 8 == 0 && COUT % 8 == 0, "channel counts are multiples of 8");
     extern __shared__ __align__(16) unsigned char conv_smem[];
     bf16 *sw = reinterpret_cast<bf16 *>(conv_smem);
     constexpr int NW = 27 * COUT * CIN;
@@ -107,6 +116,23 @@ __global__ void __launch_bounds__(128) k_conv3d(const bf16 *__restrict__ x, cons
                     const unsigned b0 = ld_pair(pw), b1 = ld_pair(pw + 8);
 #pragma unroll
                     for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], a[i], b0, b1);
+                }
+            }
+            if (CIN % 16 == 8) {  // the last 8 input channels: k8 steps
+                const int c0 = (CIN / 16) * 16 + 2 * t;
+                unsigned a[2][2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int xa = xs + 16 * i + g + dx, xb = xa + 8;
+                    const bool oka = row_ok && xa >= 0 && xa < X, okb = row_ok && xb >= 0 && xb < X;
+                    a[i][0] = oka ? ld_pair(xv + (rbase + (oka ? xa : 0)) * CIN + c0) : 0u;
+                    a[i][1] = okb ? ld_pair(xv + (rbase + (okb ? xb : 0)) * CIN + c0) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < COUT / 8; ++j) {
+                    const unsigned b0 = ld_pair(sw + (off * COUT + j * 8 + g) * CIN + c0);
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) mma_bf16_k8(acc[i][j], a[i][0], a[i][1], b0);
                 }
             }
         }
@@ -192,6 +218,121 @@ __global__ void __launch_bounds__(256) k_conv3d_wgrad(const bf16 *__restrict__ x
     for (int p = 0; p < PER; ++p) {
         const int pi = threadIdx.x + p * 256;
         if (pi < NP) atomicAdd(dw + (size_t)off * NP + pi, acc[p]);
+    }
+}
+
+// ldmatrix .x4 / .x2 with transposition: each lane passes the shared-memory
+// address of one 16-byte row (lanes 8j .. 8j+7 address the rows of matrix j).
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned &r0, unsigned &r1, const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+// Row stride (bytes) of a staged [voxel][C] BF16 tile: C*2 rounded so that
+// stride / 16 is odd, which keeps the 8 rows of an ldmatrix on distinct banks.
+__host__ __device__ constexpr int tile_stride(int C) { return ((C / 8) % 2 == 1) ? C * 2 : C * 2 + 16; }
+
+constexpr int WG_V = 64;           // voxels (along x) per work item
+constexpr int WG_ROWS = WG_V + 2;  // with the x halo
+
+// Weight gradient on tensor cores: for each offset d, dw[d]^T = X_d^T GY
+// (M = CIN input channels, N = COUT output channels, K = voxels), X_d the
+// input shifted by d.  A work item is WG_V voxels of one (n, z, y) row; the
+// CTA stages the gradient tile and the nine halo'd input rows (dz, dy) in
+// shared memory; warp w = (dz, dy) accumulates the three dx offsets in
+// registers over all of the CTA's items, then adds them to dw.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(288) k_conv3d_wgrad_mma(const bf16 *__restrict__ x, const bf16 *__restrict__ gy,
+                                                          float *__restrict__ dw, int N, int Z, int Y, int X) {
+    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "tile shapes");
+    constexpr int SX = tile_stride(CIN), SG = tile_stride(COUT);
+    constexpr int MT = CIN / 16, NT = COUT / 8;
+    extern __shared__ __align__(16) unsigned char wg_smem[];
+    unsigned char *sxt = wg_smem;                        // [9][WG_ROWS] rows of SX bytes
+    unsigned char *sgt = wg_smem + 9 * WG_ROWS * SX;     // [WG_V] rows of SG bytes
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wdz = warp / 3 - 1, wdy = warp % 3 - 1;
+    float acc[3][MT][NT][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][m][n][q] = 0.f;
+    const int ntx = (X + WG_V - 1) / WG_V;
+    const long long items = (long long)N * Z * Y * ntx;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const long long row = it / ntx;
+        const int x0 = (int)(it - row * ntx) * WG_V;
+        const int yy0 = (int)(row % Y);
+        const long long nz = row / Y;
+        const int z0 = (int)(nz % Z);
+        const long long n = nz / Z;
+        __syncthreads();  // the previous item's tiles are no longer read
+        // input rows (dz, dy) with voxels x0 - 1 .. x0 + WG_V, 16 bytes per copy
+        constexpr int XC = CIN / 8;
+        for (int e = threadIdx.x; e < 9 * WG_ROWS * XC; e += blockDim.x) {
+            const int c = e % XC, r = (e / XC) % WG_ROWS, k = e / (XC * WG_ROWS);
+            const int zz = z0 + k / 3 - 1, yy = yy0 + k % 3 - 1, xx = x0 + r - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (zz >= 0 && zz < Z && yy >= 0 && yy < Y && xx >= 0 && xx < X)
+                v = *reinterpret_cast<const uint4 *>(x + (((size_t)(n * Z + zz) * Y + yy) * X + xx) * CIN + 8 * c);
+            *reinterpret_cast<uint4 *>(sxt + (k * WG_ROWS + r) * SX + 16 * c) = v;
+        }
+        constexpr int GC = COUT / 8;
+        for (int e = threadIdx.x; e < WG_V * GC; e += blockDim.x) {
+            const int c = e % GC, r = e / GC, xx = x0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (xx < X) v = *reinterpret_cast<const uint4 *>(gy + ((size_t)row * X + xx) * COUT + 8 * c);
+            *reinterpret_cast<uint4 *>(sgt + r * SG + 16 * c) = v;
+        }
+        __syncthreads();
+        const unsigned char *xrow = sxt + ((wdz + 1) * 3 + (wdy + 1)) * WG_ROWS * SX;
+        const int lr = lane & 7, lm = lane >> 3;  // row within a matrix, matrix index
+#pragma unroll
+        for (int k0 = 0; k0 < WG_V; k0 += 16) {
+            // B fragments (k = voxel, n = output channel) from the gradient tile
+            unsigned b[NT][2];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+                ldsm_x2_t(b[nt][0], b[nt][1], sgt + (k0 + lr + 8 * (lm & 1)) * SG + nt * 16);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {  // dx = a - 1: voxel v reads input row v + dx (+1 for the halo)
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    unsigned af[4];
+                    // matrices: (k 0-7, m 0-7), (k 0-7, m 8-15), (k 8-15, m 0-7), (k 8-15, m 8-15)
+                    ldsm_x4_t(af, xrow + (k0 + a + lr + 8 * (lm >> 1)) * SX + mt * 32 + 16 * (lm & 1));
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[a][mt][nt], af, b[nt][0], b[nt][1]);
+                }
+            }
+        }
+    }
+    // acc[a][mt][nt]: (m = input channel mt*16 + g (+8), n = output channel nt*8 + 2t (+1))
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int off = ((wdz + 1) * 3 + (wdy + 1)) * 3 + a;
+        float *d = dw + (size_t)off * COUT * CIN;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int i = mt * 16 + g, o = nt * 8 + 2 * t;
+                atomicAdd(d + (size_t)o * CIN + i, acc[a][mt][nt][0]);
+                atomicAdd(d + (size_t)(o + 1) * CIN + i, acc[a][mt][nt][1]);
+                atomicAdd(d + (size_t)o * CIN + i + 8, acc[a][mt][nt][2]);
+                atomicAdd(d + (size_t)(o + 1) * CIN + i + 8, acc[a][mt][nt][3]);
+            }
     }
 }
 
@@ -354,26 +495,42 @@ cudaError_t launch_conv3d(const void *x, const float *w, const float *bias, void
     return cudaSuccess;
 }
 
+template <int CIN, int COUT>
+cudaError_t run_wgrad_mma(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, cudaStream_t s) {
+    const int smem = 9 * WG_ROWS * tile_stride(CIN) + WG_V * tile_stride(COUT);
+    auto kern = k_conv3d_wgrad_mma<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 288, smem);
+    if (e != cudaSuccess) return e;
+    const long long items = (long long)N * Z * Y * ((X + WG_V - 1) / WG_V);
+    long long grid = (long long)sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (grid > items) grid = items;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<(unsigned)grid, 288, smem, s>>>((const bf16 *)x, (const bf16 *)gy, dw, N, Z, Y, X);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv3d_wgrad(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, int cin,
                                 int cout, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * 27 * cin * cout, s);
     if (e != cudaSuccess) return e;
+    if (cin == 16 && cout == 32) return run_wgrad_mma<16, 32>(x, gy, dw, N, Z, Y, X, s);
+    if (cin == 32 && cout == 32) return run_wgrad_mma<32, 32>(x, gy, dw, N, Z, Y, X, s);
+    if (cin == 32 && cout == 8) return run_wgrad_mma<32, 8>(x, gy, dw, N, Z, Y, X, s);
+    if (cin == 32 && cout == 16) return run_wgrad_mma<32, 16>(x, gy, dw, N, Z, Y, X, s);
+    if (cin == 16 && cout == 16) return run_wgrad_mma<16, 16>(x, gy, dw, N, Z, Y, X, s);
+    // cin = 8 (no 16-row tile): FP32 CUDA-core kernel
     const long long nrows = (long long)N * Z * Y;
     const int rows = (int)((nrows + 151) / 152 > 0 ? (nrows + 151) / 152 : 1);  // ~152 CTAs per offset
     dim3 grid((unsigned)((nrows + rows - 1) / rows), 27);
-#define TG_WG_CASE(CI, CO)                                                                                     \
-    if (cin == CI && cout == CO) {                                                                             \
-        k_conv3d_wgrad<CI, CO><<<grid, 256, 0, s>>>((const bf16 *)x, (const bf16 *)gy, dw, N, Z, Y, X, rows);  \
-        count_launch();                                                                                        \
-        return cudaGetLastError();                                                                             \
+    if (cin == 8 && cout == 32) {
+        k_conv3d_wgrad<8, 32><<<grid, 256, 0, s>>>((const bf16 *)x, (const bf16 *)gy, dw, N, Z, Y, X, rows);
+        count_launch();
+        return cudaGetLastError();
     }
-    TG_WG_CASE(16, 32)
-    TG_WG_CASE(32, 32)
-    TG_WG_CASE(32, 8)
-    TG_WG_CASE(32, 16)
-    TG_WG_CASE(8, 32)
-    TG_WG_CASE(16, 16)
-#undef TG_WG_CASE
     return cudaErrorInvalidValue;
 }
 

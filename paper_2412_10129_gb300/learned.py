@@ -250,7 +250,7 @@ def train(net: LearnedGradient, geo, seeds, steps: int = 10, batch: int = 2, lr:
             opt.zero_grad(set_to_none=True)
             loss.backward()
             opt.step()
-            losses.append(float(loss))
+            losses.append(float(loss.detach()))
             if log is not None:
                 log(len(losses), losses[-1])
     return losses

@@ -7,9 +7,11 @@ final rounding of BF16 outputs (half a BF16 ulp, 2^-9 relative, plus the
 accumulation error).  The data-fit gradient A^T(Ax - b) is checked against
 the oracle's projector pair (2e-5 relative L2: one forward and one
 backprojection, 1e-5 each).  A whole learned step and its gradient are
-checked against oracle.learned; the network's activations are BF16 there
-(the oracle mirrors the forward rounding), so the bound is 1e-2 relative L2
-(ten BF16 roundings of about 2^-9 each along the chain, with margin).
+checked against oracle.learned with the network's BF16 roundings mirrored
+(activations forward, layer-input gradients backward): without them the
+BF16 gradient differs from the FP64 one by about 8 % through cancellation
+in the sums; with them what is left is FP32 summation order and the BF16
+rounding decisions it flips (bounds in the test).
 Training reduces the loss and beats the untrained scheme on held-out
 phantoms; batched and ragged (uneven-size) inference reproduce the
 one-volume results bit for bit."""
@@ -190,19 +192,41 @@ def _small_problem(seed=0, n=24):
     return g, b, x0, gt
 
 
-def test_learned_step_matches_oracle():
+@pytest.mark.parametrize("signed", [False, True])
+def test_learned_step_matches_oracle(signed):
+    """One step and its gradient against oracle.learned (BF16 roundings
+    mirrored).  With non-negative inputs and weights, biases below zero (so
+    that the ReLU masks cut) and a non-negative output gradient no sum
+    cancels, and
+    what is left is FP32 summation order and the BF16 rounding decisions it
+    flips (each one 2^-8 of a value): 5e-3.  With weights and gradients
+    of both signs the sums cancel, and then inputs that differ by 1e-6
+    relative already move the BF16 gradient by about 1.4 % (measured with
+    the oracle alone), so the bound is 5e-2."""
     L = lm()
     g, b, x0, gt = _small_problem(seed=3)
-    net = L.LearnedGradient(seed=1, init_scale=1.0).cuda()
-    with torch.no_grad():                 # make every weight matter
-        net.weights[-1].add_(0.05 * torch.randn(net.weights[-1].shape, generator=torch.Generator().manual_seed(2))
-                             .cuda())
+    net = L.LearnedGradient(seed=1, gd_init=False, init_scale=1.0).cuda()
+    gen = torch.Generator().manual_seed(2)
+    with torch.no_grad():
+        for li, (w, c) in enumerate(zip(net.weights, net.biases)):
+            cin = 2 if li == 0 else w.shape[2]
+            if not signed:
+                w.copy_(torch.rand(w.shape, generator=gen).cuda() * (2.0 / (27 * cin)))
+                c.copy_(-0.3 * torch.rand(c.shape, generator=gen).cuda())
+            else:
+                c.copy_(0.1 * torch.randn(c.shape, generator=gen).cuda())
+        net.weights[0][:, :, 2:] = 0.0
         net.weights[-1][:, 1:, :] = 0.0
+    tol = 5e-2 if signed else 5e-3
+    if not signed:                     # x >= 0 and b = 0 make A^T(Ax - b) >= 0 as well
+        x0 = gt + 0.01
+        b = torch.zeros_like(b)
     eta = 1.0 / lm().operator_norm_sq(g)
     sx = 1.0 / L.MU_REF
     x = x0.clone().requires_grad_(True)
     xn = net.step(x[None], b[None], g, eta)[0]
-    gbar = torch.from_numpy(np.random.default_rng(4).standard_normal(g.vol_shape).astype(np.float32)).cuda()
+    gb = np.random.default_rng(4).standard_normal(g.vol_shape).astype(np.float32)
+    gbar = torch.from_numpy(gb if signed else np.abs(gb)).cuda()
     torch.sum(xn * gbar).backward()
     Ws = [to_oracle_w(oconv.bf16_round(w.detach().cpu().numpy())) for w in net.weights]
     Bs = [c.detach().cpu().numpy().astype(np.float64) for c in net.biases]
@@ -210,22 +234,24 @@ def test_learned_step_matches_oracle():
     bo = b.cpu().numpy().astype(np.float64)
     ref, _ = olearned.step(g, xo, bo, Ws, Bs, sx, sx * eta, 1.0 / sx, round_act=oconv.bf16_round)
     upd = xn.detach().cpu().numpy() - xo
-    assert rel_l2(upd, ref - xo) <= 1e-2
-    gx, dWs, dBs = olearned.step_backward(g, xo, bo, Ws, Bs, sx, sx * eta, 1.0 / sx, gbar.cpu().numpy())
-    assert rel_l2(x.grad.cpu().numpy() - gbar.cpu().numpy(), gx - gbar.cpu().numpy()) <= 1e-2
+    errs = {"update": rel_l2(upd, ref - xo)}
+    gx, dWs, dBs = olearned.step_backward(g, xo, bo, Ws, Bs, sx, sx * eta, 1.0 / sx, gbar.cpu().numpy(),
+                                          round_act=oconv.bf16_round)
+    errs["x"] = rel_l2(x.grad.cpu().numpy() - gbar.cpu().numpy(), gx - gbar.cpu().numpy())
     for li in range(5):
         dw = to_oracle_w(net.weights[li].grad.cpu().numpy())
+        rw = dWs[li]
         if li == 0:
-            dw, rw = dw[:, :, :, :2], dWs[li][:, :, :, :2]   # padded input channels carry zeros
-        else:
-            rw = dWs[li]
+            dw, rw = dw[:, :, :, :2], rw[:, :, :, :2]   # padded input channels carry zeros
         if li == 4:
-            dw, rw = dw[..., :1], rw[..., :1]                 # padded output channels are unused
-        assert rel_l2(dw, rw) <= 1e-2, li
-        db = net.biases[li].grad.cpu().numpy()
+            dw, rw = dw[..., :1], rw[..., :1]           # padded output channels are unused
+        errs[f"w{li}"] = rel_l2(dw, rw)
+        db, rb = net.biases[li].grad.cpu().numpy(), dBs[li]
         if li == 4:
-            db, dBs[li] = db[:1], dBs[li][:1]
-        assert rel_l2(db, dBs[li]) <= 1e-2, li
+            db, rb = db[:1], rb[:1]
+        errs[f"b{li}"] = rel_l2(db, rb)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, errs
 
 
 def test_gd_init_is_gradient_descent():
@@ -267,10 +293,12 @@ def test_batched_and_ragged_inference_match_single():
 
 
 def test_training_improves_on_the_untrained_scheme():
-    """A short training run (32^3 at 8 mm, 15 angles, 48 phantoms) lowers the
-    loss, and the trained scheme beats the untrained one (plain gradient
-    descent) on held-out phantoms, judged by PSNR and by the oracle's FP64
-    data residual staying of the same order."""
+    """A short training run (32^3 at 8 mm, 15 angles, 100 batches of 2
+    phantoms) lowers the loss and lifts the held-out PSNR well above both
+    the untrained scheme (gradient descent from FDK) and the best plain
+    CGLS iterate; the oracle's FP64 data residual of the result stays of the
+    order of the FDK start's (the network is trained for the image, not for
+    the data fit)."""
     L = lm()
     g = inputs.circular_geometry((32,) * 3, (8.0,) * 3, (64, 64), (6.4, 6.4), 15, 1000.0, 1536.0)
     torch.manual_seed(0)
@@ -283,11 +311,12 @@ def test_training_improves_on_the_untrained_scheme():
             return np.mean([L.psnr(net(x0, b, g, steps=5, eta=eta), gt) for b, x0, gt in test])
 
     before = score()
-    losses = L.train(net, g, range(1000, 1048), steps=5, batch=2, lr=2e-3, epochs=2)
+    losses = L.train(net, g, range(1000, 1200), steps=5, batch=2, lr=3e-4)
     after = score()
-    assert np.mean(losses[-6:]) < 0.9 * np.mean(losses[:6])
-    assert after > before + 0.5
+    assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
+    assert after > before + 3.0
     b, x0, gt = test[0]
+    assert L.psnr(net(x0, b, g, steps=5, eta=eta).detach(), gt) > L.cgls_best(g, b, gt, 30)[0] + 1.0
     with torch.no_grad():
         x = net(x0, b, g, steps=5, eta=eta)
     res = np.linalg.norm(oracle.forward(g, x.cpu().numpy()) - b.cpu().numpy().astype(np.float64))
