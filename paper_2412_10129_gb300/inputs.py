@@ -283,6 +283,15 @@ def random_projections(geo: Geometry, seed: int, dtype=np.float32) -> np.ndarray
     return np.random.default_rng(seed).random(geo.proj_shape).astype(dtype)
 
 
+def poisson_noise_device(b, I0: float, seed: int):
+    """poisson_noise for a torch tensor on its own device (a seeded torch
+    generator there; a different stream of numbers than the numpy version)."""
+    import torch
+    gen = torch.Generator(device=b.device).manual_seed(int(seed))
+    counts = torch.poisson(I0 * torch.exp(-b.double()), generator=gen)
+    return (-torch.log(torch.clamp(counts, min=1.0) / I0)).to(b.dtype)
+
+
 def poisson_noise(b: np.ndarray, I0: float, seed: int) -> np.ndarray:
     """Transmission noise on line integrals b: counts ~ Poisson(I0 e^-b),
     returned as -ln(max(counts, 1) / I0)."""

@@ -90,7 +90,10 @@ class LearnedGradient(torch.nn.Module):
     def step(self, x, b, geo, eta: float):
         """One learned-gradient step on a batch x [B, nz, ny, nx] (FP32, CUDA)."""
         sx = 1.0 / MU_REF
-        return _LGStep.apply(x, b, (geo, sx, sx * eta, 1.0 / sx), *self.params())
+        cfg = (geo, sx, sx * eta, 1.0 / sx)
+        if not torch.is_grad_enabled():
+            return _lg_step_infer(x, b, cfg, self.weights, self.biases)
+        return _LGStep.apply(x, b, cfg, *self.params())
 
     def forward(self, x0, b, geo, steps: int = 10, eta: float | None = None, checkpoint: bool = False):
         """x_K of the unrolled scheme from x0 [(B,) nz, ny, nx] and data b [(B,) nA, nv, nu]."""
@@ -118,6 +121,17 @@ def _conv_stack(inp, ws, bs, keep: bool):
             acts.append(h)
     out = tg.conv3d(h, ws[-1], bs[-1], relu=False, out_f32=True)
     return out, acts
+
+
+def _lg_step_infer(x, b, cfg, ws, bs):
+    """The step without autograd: no activation is kept."""
+    geo, sx, sg, so = cfg
+    x = x.contiguous()
+    grad = tg.gradient(geo, x, b.contiguous())
+    inp = tg.lg_pack(x, grad, IN_CH, sx, sg)
+    del grad
+    out, _ = _conv_stack(inp, [w.detach() for w in ws], [c.detach() for c in bs], keep=False)
+    return tg.lg_update(x, out, so)
 
 
 class _LGStep(torch.autograd.Function):
@@ -211,16 +225,31 @@ def infer_ragged(net: LearnedGradient, geos, bs, x0s, steps: int = 10, etas=None
 # Training data and training loop.
 # ---------------------------------------------------------------------------
 
-def make_sample(geo, seed: int, I0: float = 1e4, device="cuda"):
+def make_sample(geo, seed: int, I0: float = 1e4, device="cuda", phantom=None):
     """(b, x0, x_true) for one seeded phantom: b = noisy line integrals
-    (Siddon projection of the voxelised phantom, Poisson noise at I0),
-    x0 = FDK of b, x_true the phantom."""
-    gt = torch.from_numpy(inputs.learned_phantom(geo, seed)).to(device)
-    clean = tg.forward(geo, gt, "siddon")
-    noisy = inputs.poisson_noise(clean.cpu().numpy(), I0, seed + 1_000_003)
-    b = torch.from_numpy(noisy).to(device)
+    (Siddon projection of the voxelised phantom, Poisson noise at I0 drawn on
+    the device), x0 = FDK of b, x_true the phantom.  ``phantom`` may hold the
+    voxelised phantom already (e.g. from a prefetching thread)."""
+    if phantom is None:
+        phantom = inputs.learned_phantom(geo, seed)
+    gt = torch.from_numpy(phantom).to(device)
+    b = inputs.poisson_noise_device(tg.forward(geo, gt, "siddon"), I0, seed + 1_000_003)
     x0 = tg.fdk(geo, b)
     return b, x0, gt
+
+
+def samples(geo, seeds, I0: float = 1e4, device="cuda", prefetch: int = 4):
+    """make_sample over ``seeds``, voxelising the next phantoms on host
+    threads while the GPU works on the current one."""
+    from concurrent.futures import ThreadPoolExecutor
+    seeds = list(seeds)
+    with ThreadPoolExecutor(max_workers=2) as pool:
+        futs = [pool.submit(inputs.learned_phantom, geo, s) for s in seeds[:prefetch]]
+        for i, s in enumerate(seeds):
+            ph = futs[i].result()
+            if i + prefetch < len(seeds):
+                futs.append(pool.submit(inputs.learned_phantom, geo, seeds[i + prefetch]))
+            yield make_sample(geo, s, I0, device, phantom=ph)
 
 
 def psnr(x: torch.Tensor, gt: torch.Tensor) -> float:
@@ -238,9 +267,11 @@ def train(net: LearnedGradient, geo, seeds, steps: int = 10, batch: int = 2, lr:
     opt = torch.optim.Adam(net.parameters(), lr=lr)
     losses = []
     seeds = list(seeds)
+    nb = len(seeds) // batch
     for _ in range(epochs):
-        for i in range(0, len(seeds) - batch + 1, batch):
-            smp = [make_sample(geo, s, I0, device) for s in seeds[i:i + batch]]
+        it = samples(geo, seeds[:nb * batch], I0, device)
+        for _ in range(nb):
+            smp = [next(it) for _ in range(batch)]
             b = torch.stack([s[0] for s in smp])
             x0 = torch.stack([s[1] for s in smp])
             gt = torch.stack([s[2] for s in smp])
