@@ -228,6 +228,14 @@ tg_status tg_lg_unpack(const void *in, int channels, float *a, float *b, size_t 
 tg_status tg_lg_update(const float *x, const float *net, float *xnext, size_t nvox, int net_channels, float so,
                        void *stream);
 
+/* Waits for `stream`, then reports (and clears) the device-side wait flag
+ * of the tensor-core kernels: TG_ERR_TIMEOUT when one of their bounded
+ * waits gave up since the last call (their outputs are then invalid),
+ * TG_OK otherwise.  Kernels that wait on one another inside a launch
+ * (producer, MMA and epilogue roles of the tcgen05 convolutions) never
+ * spin without a limit; this is how a caller learns that a limit ran out. */
+tg_status tg_device_status(void *stream);
+
 /* Bytes of device scratch a call would take (op: 0 forward, 1 backproject,
  * 2 fdk, 3 sirt, 4 ossart, 5 cgls; blocksize only for ossart). */
 tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int batch, int blocksize,

@@ -16,6 +16,9 @@
 // dw[d, o, i] = sum_v x[v + d, i] gy[v, o] accumulates in FP32.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
+#include <cstring>
+
 #include "tg_internal.cuh"
 
 namespace tg {
@@ -447,8 +450,18 @@ cudaError_t dispatch_conv(const void *x, const float *w, const float *bias, void
 
 }  // namespace
 
+// The tensor-core kernels (tg_conv_tc.cu) take the channel pairs they
+// support unless TG_CONV_IMPL=mma selects the mma.sync kernel below
+// (kept for 8-channel inputs and for comparisons).
+bool use_tc(const void *x, int cin, int cout) {
+    const char *env = getenv("TG_CONV_IMPL");
+    if (env && strcmp(env, "mma") == 0) return false;
+    return ((uintptr_t)x & 15u) == 0 && conv_tc_supported(cin, cout);
+}
+
 cudaError_t launch_conv3d_ragged(const void *x, const float *w, const float *bias, void *y, const int *dims,
                                  int nvol, int cin, int cout, int relu, int out_f32, cudaStream_t s) {
+    if (use_tc(x, cin, cout)) return launch_conv3d_tc_ragged(x, w, bias, y, dims, nvol, cin, cout, relu, out_f32, s);
     size_t vox = 0;  // voxels before the current chunk
     for (int v0 = 0; v0 < nvol; v0 += MAXV) {
         ConvTable tab{};
@@ -478,6 +491,7 @@ cudaError_t launch_conv3d_ragged(const void *x, const float *w, const float *bia
 
 cudaError_t launch_conv3d(const void *x, const float *w, const float *bias, void *y, int N, int Z, int Y, int X, int cin,
                           int cout, int relu, int out_f32, cudaStream_t s) {
+    if (use_tc(x, cin, cout)) return launch_conv3d_tc(x, w, bias, y, N, Z, Y, X, cin, cout, relu, out_f32, s);
     int dims[3 * MAXV];
     for (int k = 0; k < MAXV; ++k) {
         dims[3 * k] = Z;

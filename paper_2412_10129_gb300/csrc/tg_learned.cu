@@ -91,4 +91,12 @@ tg_status tg_lg_update(const float *x, const float *net, float *xnext, size_t nv
     return st(launch_lg_update(x, net, xnext, nvox, net_channels, so, (cudaStream_t)stream));
 }
 
+tg_status tg_device_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return TG_ERR_CUDA;
+    int flag = 0;
+    if (read_tc_error(&flag) != cudaSuccess) return TG_ERR_CUDA;
+    return flag ? TG_ERR_TIMEOUT : TG_OK;
+}
+
 }  // extern "C"

@@ -307,3 +307,46 @@ def timed(fn, reps: int = 3):
         torch.cuda.synchronize()
         ts.append(time.perf_counter() - t0)
     return float(np.median(ts))
+
+
+def conv_benchmark(n: int = 256, reps: int = 5, layers=((32, 32), (16, 32), (32, 8))):
+    """Device time of each convolution kernel on an n^3 volume (CUDA events):
+    forward, input gradient and weight gradient per (cin, cout) pair, with
+    their FLOP rates (2 * 27 * cin * cout per voxel)."""
+    out = []
+    for cin, cout in layers:
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn((1, n, n, n, cin), device="cuda", generator=gen).to(torch.bfloat16)
+        gy = torch.randn((1, n, n, n, cout), device="cuda", generator=gen).to(torch.bfloat16)
+        w = torch.randn((27, cout, cin), device="cuda", generator=gen) * 0.05
+        ops = (("forward", lambda: tg.conv3d(x, w, None, relu=True)),
+               ("backward_data", lambda: tg.conv3d_backward_data(gy, w)),
+               ("backward_weight", lambda: tg.conv3d_backward_weight(x, gy)))
+        for name, fn in ops:
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out.append({"cin": cin, "cout": cout, "op": name, "ms": ms,
+                        "tflops": 2 * 27 * cin * cout * n ** 3 / ms / 1e9})
+        tg.device_status()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="learned-gradient kernels: convolution timings")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=5)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    for row in conv_benchmark(a.n, a.reps):
+        print(json.dumps(row), flush=True)

@@ -86,6 +86,7 @@ def load():
             "tg_lg_unpack": [_VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, ctypes.c_float, ctypes.c_float,
                              ctypes.c_int, _VP],
             "tg_lg_update": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_float, _VP],
+            "tg_device_status": [_VP],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -310,6 +311,16 @@ def count_samples(geo, method: str = "interp", stream=None) -> int:
     s = getattr(stream, "cuda_stream", stream)
     _check("tg_count_samples", load().tg_count_samples(G.ref, G.ang, G.n, _METHOD_FP[method], ctypes.byref(out), s))
     return int(out.value)
+
+
+def device_status(stream=None) -> None:
+    """Waits for the stream and raises TgError(TG_ERR_TIMEOUT) when a
+    bounded device-side wait of the tensor-core kernels gave up."""
+    torch = _torch()
+    st = getattr(stream, "cuda_stream", stream)
+    if st is None and torch.cuda.is_available():
+        st = torch.cuda.current_stream().cuda_stream
+    _check("tg_device_status", load().tg_device_status(st))
 
 
 def launch_count() -> int:

@@ -83,6 +83,52 @@ def test_conv_forward_matches_oracle(cin, cout, shape):
     assert rel_l2(y, oconv.conv3d(xo, wo)) <= 1e-5
 
 
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 8), (32, 16), (16, 16)])
+def test_tensor_core_and_mma_paths_agree(cin, cout, monkeypatch):
+    """The tcgen05 kernels (default) and the mma.sync kernels
+    (TG_CONV_IMPL=mma) both match the oracle; their FP32 outputs differ
+    only by summation order."""
+    rng = np.random.default_rng(cin + 7 * cout)
+    x, xo = bf16_input(rng, (2, 6, 5, 300, cin))
+    w, wo = rand_w(rng, cin, cout)
+    bias = torch.from_numpy(rng.standard_normal(cout).astype(np.float32)).cuda()
+    ref = oconv.conv3d(xo, wo, bias.cpu().numpy(), relu=True)
+    y_tc = tg.conv3d(x, w, bias, relu=True, out_f32=True)
+    tg.device_status()
+    monkeypatch.setenv("TG_CONV_IMPL", "mma")
+    y_mma = tg.conv3d(x, w, bias, relu=True, out_f32=True)
+    monkeypatch.delenv("TG_CONV_IMPL")
+    for y in (y_tc, y_mma):
+        assert rel_l2(y.cpu().numpy(), ref) <= 1e-5
+        assert max_rel(y.cpu().numpy(), ref) <= 1e-4
+    assert rel_l2(y_tc.cpu().numpy(), y_mma.cpu().numpy()) <= 1e-5
+    tg.device_status()
+
+
+def test_tensor_core_conv_repeats_bit_for_bit():
+    """Many items per CTA (each accumulator buffer reused many times) and
+    several volumes per launch: repeated launches agree bit for bit and
+    with the oracle on every voxel (a missing ordering between the MMAs,
+    the row shifts and the epilogue would corrupt whole rows at random)."""
+    rng = np.random.default_rng(29)
+    dims = [(9, 40, 250), (7, 33, 130), (11, 21, 37)]
+    xs = [bf16_input(rng, (1,) + d + (32,)) for d in dims]
+    w, wo = rand_w(rng, 32, 32)
+    packed = torch.cat([x.reshape(-1, 32) for x, _ in xs]).contiguous()
+    first = tg.conv3d_ragged(packed, dims, w, None, relu=False, out_f32=True)
+    for _ in range(4):
+        assert torch.equal(tg.conv3d_ragged(packed, dims, w, None, relu=False, out_f32=True), first)
+    off = 0
+    for (x, xo), d in zip(xs, dims):
+        n = int(np.prod(d))
+        ref = oconv.conv3d(xo, wo).reshape(-1, 32)
+        y = first[off:off + n].cpu().numpy()
+        assert max_rel(y, ref) <= 1e-4
+        assert torch.equal(tg.conv3d(x, w, None, out_f32=True).reshape(-1, 32), first[off:off + n])
+        off += n
+    tg.device_status()
+
+
 def test_conv_single_voxel_and_thin_volumes():
     rng = np.random.default_rng(5)
     for shape in [(1, 1, 1, 1), (1, 1, 1, 129), (3, 2, 1, 3), (1, 1, 9, 1)]:
