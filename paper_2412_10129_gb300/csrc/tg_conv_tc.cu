@@ -3,12 +3,15 @@
 // by TMA.  Same layouts and results as k_conv3d in tg_conv.cu (BF16 inputs
 // and weights, FP32 accumulation); used for cin in {16, 32}.
 //
-// Work item: 120 consecutive output voxels along x of one (volume, z, y)
-// row, as four quarters of 30.  For each of the nine (dz, dy) input rows the
-// producer stages, per quarter q, the 32 voxels x0 + 30 q - 1 .. x0 + 30 q + 30
-// with all their channels (TMA boxes; zero fill outside the volume = the
-// convolution's zero padding; 64- or 32-byte swizzle = the tensor cores'
-// K-major canonical layout) as MMA rows 32 q .. 32 q + 31.  The three x taps
+// Work: the output is cut into segments of 30 consecutive voxels along x of
+// one (volume, z, y) row; a work item is four consecutive segments, one per
+// 32-row quarter of the MMA (segments of different rows or volumes may share
+// an item, so short rows waste little).  For each of the nine (dz, dy)
+// offsets the producer stages, per quarter, the 32 input voxels x0 - 1 ..
+// x0 + 30 of the segment's row (z + dz, y + dy) with all their channels (TMA
+// boxes; zero fill outside the volume = the convolution's zero padding; 64-
+// or 32-byte swizzle = the tensor cores' K-major canonical layout) as MMA
+// rows 32 q .. 32 q + 31.  The three x taps
 // go into the MMA's N dimension: with B = [W(dz,dy,-1) W(dz,dy,0)
 // W(dz,dy,+1)] (N = 3 cout) one tcgen05.mma per 16-channel slice gives
 //     D[r][dx, o] = sum_{dz,dy} sum_c x(z+dz, y+dy, staged voxel r)[c] w(dz,dy,dx)[o][c],
@@ -44,8 +47,7 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int TC_M = 128;                     // staged voxels per input row (MMA M)
-constexpr int TC_Q = 30;                      // output voxels per 32-row quarter
-constexpr int TC_OUT = 4 * TC_Q;              // output voxels per item
+constexpr int TC_Q = 30;                      // output voxels per segment (32-row quarter)
 constexpr int TC_STAGES = 6;
 constexpr int TC_MAXV = 32;                   // volumes per launch
 constexpr int TC_MAXM = 16;                   // tensor maps per launch
@@ -55,7 +57,7 @@ constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 struct TcParams {
     CUtensorMap maps[TC_MAXM];
     int nvol;
-    int item0[TC_MAXV + 1];
+    int seg0[TC_MAXV + 1];     // first segment of each volume; seg0[nvol] = all segments
     int Z[TC_MAXV], Y[TC_MAXV], X[TC_MAXV];
     int map_of[TC_MAXV], n_of[TC_MAXV];
     long long vox0[TC_MAXV];
@@ -177,21 +179,25 @@ __device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo,
 
 struct Item {
     int v, n, z, y, x0;
+    bool valid;
 };
 
-__device__ __forceinline__ Item decode(const TcParams &p, int it) {
+// Segment `sg` (30 outputs of one row): volume, row and first voxel.
+__device__ __forceinline__ Item decode(const TcParams &p, int sg) {
+    Item r;
+    r.valid = sg < p.seg0[p.nvol];
+    if (!r.valid) sg = 0;
     int lo = 0, hi = p.nvol - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (p.item0[mid] <= it) lo = mid;
+        if (p.seg0[mid] <= sg) lo = mid;
         else hi = mid - 1;
     }
-    Item r;
     r.v = lo;
-    const int ntx = (p.X[lo] + TC_OUT - 1) / TC_OUT;
-    const int local = it - p.item0[lo];
-    const int row = local / ntx;
-    r.x0 = (local - row * ntx) * TC_OUT;
+    const int nsx = (p.X[lo] + TC_Q - 1) / TC_Q;
+    const int local = sg - p.seg0[lo];
+    const int row = local / nsx;
+    r.x0 = (local - row * nsx) * TC_Q;
     r.y = row % p.Y[lo];
     r.z = row / p.Y[lo];
     r.n = p.n_of[lo];
@@ -281,14 +287,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = s_tmem;
-    const int total = p.item0[p.nvol];
+    const int total = (p.seg0[p.nvol] + 3) / 4;  // work items
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
             int q = 0;
             for (int it = blockIdx.x; it < total; it += gridDim.x) {
-                const Item w = decode(p, it);
-                const CUtensorMap *map = &p.maps[p.map_of[w.v]];
+                Item w[4];
+                const CUtensorMap *map[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    w[qq] = decode(p, 4 * it + qq);
+                    if (!w[qq].valid) w[qq] = w[0];  // an unused quarter loads (and never stores) quarter 0's data
+                    map[qq] = &p.maps[p.map_of[w[qq].v]];
+                }
                 bool ok = true;
                 for (int k = 0; k < 9; ++k, ++q) {
                     const int s = q % TC_STAGES;
@@ -299,8 +311,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
                     mbar_expect_tx(full(s), S::STAGE);
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq)
-                        tma_load_5d(st0 + s * S::STAGE + qq * 32 * S::ROWB, map, full(s), 0, w.x0 + TC_Q * qq - 1,
-                                    w.y + k % 3 - 1, w.z + k / 3 - 1, w.n);
+                        tma_load_5d(st0 + s * S::STAGE + qq * 32 * S::ROWB, map[qq], full(s), 0, w[qq].x0 - 1,
+                                    w[qq].y + k % 3 - 1, w[qq].z + k / 3 - 1, w[qq].n);
                 }
                 if (!ok) break;
             }
@@ -403,9 +415,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
                 out[o] = d0[o] + d1[o] + d2[o] + bv[o];
                 if (RELU) out[o] = fmaxf(out[o], 0.f);
             }
-            const Item w = decode(p, it);
-            const int xo = w.x0 + TC_Q * sub + lane;
-            if (lane < TC_Q && xo < p.X[w.v]) {
+            const Item w = decode(p, 4 * it + sub);
+            const int xo = w.x0 + lane;
+            if (w.valid && lane < TC_Q && xo < p.X[w.v]) {
                 const size_t vox = (size_t)p.vox0[w.v] + ((size_t)w.z * p.Y[w.v] + w.y) * p.X[w.v] + xo;
                 if (OUT_F32) {
                     float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + vox * COUT);
@@ -493,7 +505,7 @@ cudaError_t run_tc(const float *w, const float *bias, void *y, const TcParams &p
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     int per_sm = smem_sm / (S::SMEM + 1024 + 64);
     per_sm = per_sm < 1 ? 1 : per_sm > 2 ? 2 : per_sm;
-    const int total = p.item0[p.nvol];
+    const int total = (p.seg0[p.nvol] + 3) / 4;
     if (total == 0) return cudaSuccess;
     long long grid = (long long)sm_count_tc() * per_sm;
     if (grid > total) grid = total;
@@ -548,12 +560,12 @@ cudaError_t launch_conv3d_tc_ragged(const void *x, const float *w, const float *
             p.map_of[k] = k;
             p.n_of[k] = 0;
             p.vox0[k] = (long long)cvox;
-            p.item0[k] = (int)items;
-            items += (long long)Z * Y * ((X + TC_OUT - 1) / TC_OUT);
+            p.seg0[k] = (int)items;
+            items += (long long)Z * Y * ((X + TC_Q - 1) / TC_Q);
             cvox += (size_t)Z * Y * X;
             if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
         }
-        p.item0[p.nvol] = (int)items;
+        p.seg0[p.nvol] = (int)items;
         void *yc = out_f32 ? (void *)((float *)y + vox * cout) : (void *)((bf16 *)y + vox * cout);
         cudaError_t e = dispatch_tc(w, bias, yc, p, cin, cout, relu, out_f32, s);
         if (e != cudaSuccess) return e;
@@ -562,7 +574,8 @@ cudaError_t launch_conv3d_tc_ragged(const void *x, const float *w, const float *
     return cudaSuccess;
 }
 
-// n volumes of Z x Y x X voxels: one 5-D tensor map per TC_MAXV volumes.
+// n volumes of Z x Y x X voxels: one 5-D tensor map per TC_MAXV volumes
+// (segments numbered volume by volume).
 cudaError_t launch_conv3d_tc(const void *x, const float *w, const float *bias, void *y, int N, int Z, int Y, int X,
                              int cin, int cout, int relu, int out_f32, cudaStream_t s) {
     const size_t per = (size_t)Z * Y * X;
@@ -572,7 +585,7 @@ cudaError_t launch_conv3d_tc(const void *x, const float *w, const float *bias, v
         p.nvol = N - n0 < TC_MAXV ? N - n0 : TC_MAXV;
         const void *xc = (const bf16 *)x + (size_t)n0 * per * cin;
         if (!make_map(&p.maps[0], xc, cin, X, Y, Z, p.nvol)) return cudaErrorInvalidValue;
-        const long long per_items = (long long)Z * Y * ((X + TC_OUT - 1) / TC_OUT);
+        const long long per_items = (long long)Z * Y * ((X + TC_Q - 1) / TC_Q);
         if (per_items * p.nvol > 0x7fffffffLL) return cudaErrorInvalidValue;
         for (int k = 0; k < p.nvol; ++k) {
             p.Z[k] = Z;
@@ -581,9 +594,9 @@ cudaError_t launch_conv3d_tc(const void *x, const float *w, const float *bias, v
             p.map_of[k] = 0;
             p.n_of[k] = k;
             p.vox0[k] = (long long)(k * per);
-            p.item0[k] = (int)(k * per_items);
+            p.seg0[k] = (int)(k * per_items);
         }
-        p.item0[p.nvol] = (int)(p.nvol * per_items);
+        p.seg0[p.nvol] = (int)(p.nvol * per_items);
         void *yc = out_f32 ? (void *)((float *)y + (size_t)n0 * per * cout)
                            : (void *)((bf16 *)y + (size_t)n0 * per * cout);
         cudaError_t e = dispatch_tc(w, bias, yc, p, cin, cout, relu, out_f32, s);
