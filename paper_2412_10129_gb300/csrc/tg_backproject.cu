@@ -90,11 +90,11 @@ __device__ __noinline__ bool ray_setup_outlined(const Angle &A, const Grid &g, i
 }
 
 constexpr int BX = 32, BY = 32, BZ = 16;              // owned voxels per brick
-constexpr int RX = BX + 2, RY = BY + 2, RZ = BZ + 2;  // with the one-voxel rim
+constexpr int RIM = 2;                                // allocated rim per side (voxels)
+constexpr int RX = BX + 2 * RIM, RY = BY + 2 * RIM, RZ = BZ + 2 * RIM;
 constexpr int PX = RX + 1;                            // row pitch (bank spreading)
 constexpr int PP = PX * RY + 9;                       // plane pitch
 constexpr int ACC_WORDS = PP * RZ;                    // one accumulator class
-constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4 + 1536 * 32;  // bytes: two classes + ray list
 constexpr float FINE = 64.f;                          // scale ratio of the classes
 constexpr int MT = 512;                               // threads per CTA
 constexpr int OWN = BX * BY * BZ / MT;                // owned voxels per thread
@@ -103,22 +103,40 @@ constexpr float MAGIC = 12582912.0f;                  // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;
 static_assert(OWN == 32 && MT == 512 && BX == 32 && BY == 32, "owned-voxel map assumes these sizes");
 
-__device__ __forceinline__ unsigned int fixq(float v) {  // round(v) for |v| < 2^22
-    return (unsigned int)(__float_as_int(v + MAGIC) - MAGIC_BITS);
+// round(a * b) for |a * b| < 2^22, rounded once (fused multiply-add of the addend)
+__device__ __forceinline__ unsigned int fixq(float a, float b) {
+    return (unsigned int)(__float_as_int(fmaf(a, b, MAGIC)) - MAGIC_BITS);
 }
 
-// A ray of the current angle with samples in the brick's region.
+// A ray of the current angle with samples in the brick's region.  Its
+// direction is rebuilt from (iu, iv) when a lane takes it, with the same
+// FP32 expressions as the forward projector.
 struct alignas(16) RayRec {
-    float gx, gy, gz;  // index-space step per sample
-    float ys;          // y, scaled to its fixed-point class
-    int ka, kc;        // samples ka..kc lie in the region (and in the volume)
-    int cls;           // 1: coarse class, 0: fine class
-    int pad;
+    unsigned int iuv;     // iu | iv << 16
+    float ys;             // y, scaled to its fixed-point class
+    int ka;               // samples ka..kc lie in the region (and in the volume)
+    unsigned int kccls;   // kc | class << 31 (1: coarse class, 0: fine class)
 };
-constexpr int RAYCAP = 1536;  // rays per shared-memory list (a chunk of candidates)
-static_assert(MATCHED_SMEM == 2 * ACC_WORDS * 4 + RAYCAP * (int)sizeof(RayRec), "shared-memory layout");
+constexpr int RAYCAP = 1024;  // rays per shared-memory list (a chunk of candidates)
+constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4 + RAYCAP * (int)sizeof(RayRec);
+static_assert(MATCHED_SMEM <= 232448, "shared memory of one CTA");
 
-// Sets up ray (iu, iv) against the region [lo, hi) and fills rec; false
+// Index-space step per sample of ray (iu, iv): the forward kernel's FP32 arithmetic.
+__device__ __forceinline__ void ray_step(const Angle &A, const Grid &g, int iu, int iv, float &gx, float &gy,
+                                         float &gz) {
+    const float fu = (float)iu, fv = (float)iv;
+    const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
+    const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
+    const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
+    const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float invL = rsqrtf(ss);
+    const float f = g.delta * invL;
+    gx = dx * f * g.idx;
+    gy = dy * f * g.idy;
+    gz = dz * f * g.idz;
+}
+
+// Sets up ray (iu, iv) against the region [lo, hi] and fills rec; false
 // when it has no sample there or carries y = 0 (it would add nothing).
 template <bool F32>
 __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const float *pa, int iu, int iv, bool edge,
@@ -133,20 +151,10 @@ __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const 
         kb0 = r.k0;
         kb1 = r.k1;
     } else {
-        // the forward kernel's FP32 arithmetic for the sample positions
-        const float fu = (float)iu, fv = (float)iv;
-        const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
-        const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
-        const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
-        const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float invL = rsqrtf(ss);
-        const float f = g.delta * invL;
         r.sx = A.Sg[0];
         r.sy = A.Sg[1];
         r.sz = A.Sg[2];
-        r.gx = dx * f * g.idx;
-        r.gy = dy * f * g.idy;
-        r.gz = dz * f * g.idz;
+        ray_step(A, g, iu, iv, r.gx, r.gy, r.gz);
     }
     float klo = (float)kb0, khi = (float)kb1;
     const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
@@ -165,16 +173,52 @@ __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const 
     if (!(khi >= klo)) return false;
     const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
     if (ka > kc) return false;
-    const bool big = fabsf(yraw) > ybig;
-    rec.gx = r.gx;
-    rec.gy = r.gy;
-    rec.gz = r.gz;
+    const bool big = F32 || fabsf(yraw) > ybig;  // FP32 sums use the first array only
+    rec.iuv = (unsigned int)iu | ((unsigned int)iv << 16);
     rec.ys = F32 ? yraw : yraw * (big ? scale : scale_f);
     rec.ka = ka;
-    rec.kc = kc;
-    rec.cls = big ? 1 : 0;
-    rec.pad = 0;
+    rec.kccls = (unsigned int)kc | (big ? 0x80000000u : 0u);
     return true;
+}
+
+// One sample's eight trilinear contributions.  A sample whose cell lies
+// outside the rimmed region (FP32 rounding at the region's edge) is clamped
+// into the two-voxel rim; the rim is never owned, so such a sample only
+// adds to voxels that are discarded.
+template <bool F32>
+__device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float gx, float gy, float gz, float sx,
+                                               float sy, float sz, float ys, int ox, int oy, int oz) {
+    const float kf = (float)k;
+    const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
+    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
+    const int lx = min(max((int)fx - ox, 0), RX - 2);
+    const int ly = min(max((int)fy - oy, 0), RY - 2);
+    const int lz = min(max((int)fz - oz, 0), RZ - 2);
+    const float wx = x - fx, wy = yy - fy, wz = z - fz;
+    const float c0 = ys * (1.f - wz), c1 = ys * wz;
+    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
+    const float ux = 1.f - wx;
+    if (F32) {
+        float *c = reinterpret_cast<float *>(accc) + lz * PP + ly * PX + lx;
+        atomicAdd(c, b00 * ux);
+        atomicAdd(c + 1, b00 * wx);
+        atomicAdd(c + PX, b01 * ux);
+        atomicAdd(c + PX + 1, b01 * wx);
+        atomicAdd(c + PP, b10 * ux);
+        atomicAdd(c + PP + 1, b10 * wx);
+        atomicAdd(c + PP + PX, b11 * ux);
+        atomicAdd(c + PP + PX + 1, b11 * wx);
+    } else {
+        unsigned int *c = accc + lz * PP + ly * PX + lx;
+        atomicAdd(c, fixq(b00, ux));
+        atomicAdd(c + 1, fixq(b00, wx));
+        atomicAdd(c + PX, fixq(b01, ux));
+        atomicAdd(c + PX + 1, fixq(b01, wx));
+        atomicAdd(c + PP, fixq(b10, ux));
+        atomicAdd(c + PP + 1, fixq(b10, wx));
+        atomicAdd(c + PP + PX, fixq(b11, ux));
+        atomicAdd(c + PP + PX + 1, fixq(b11, wx));
+    }
 }
 
 // F32: accumulate with FP32 shared atomics instead (read-modify-write loops,
@@ -188,7 +232,7 @@ __global__ void __launch_bounds__(MT, 1)
     k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
                  BpEpilogue ep, int nbx, int nby) {
     extern __shared__ unsigned int acc[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = MT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bl = blockIdx.x, b = blockIdx.y;
     const int bx = bl % nbx, by = (bl / nbx) % nby, bz = bl / (nbx * nby);
     const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
@@ -210,7 +254,8 @@ __global__ void __launch_bounds__(MT, 1)
     const float scale_f = FINE * scale, inv_scale_f = inv_scale * (1.f / FINE);
     const float ybig = gmax * (1.f / FINE);
     // owned voxel j of this thread: (lane, warp + 16 (j & 1), j >> 1)
-    const int obase = PP + (warp + 1) * PX + lane + 1;
+    const int obase = RIM * PP + (warp + RIM) * PX + lane + RIM;
+    const int ox = x0 - RIM, oy = y0 - RIM, oz = z0 - RIM;  // voxel of accumulator cell (0, 0, 0)
     float own[OWN];
 #pragma unroll
     for (int j = 0; j < OWN; ++j) own[j] = 0.f;
@@ -297,13 +342,11 @@ __global__ void __launch_bounds__(MT, 1)
                             const int idx = base + __popc(m & ((1u << lane) - 1u));
                             if (idx < nr) {
                                 const RayRec rr = rays[idx];
-                                gx = rr.gx;
-                                gy = rr.gy;
-                                gz = rr.gz;
+                                ray_step(A, g, (int)(rr.iuv & 0xffffu), (int)(rr.iuv >> 16), gx, gy, gz);
                                 ys = rr.ys;
                                 k = rr.ka;
-                                kc = rr.kc;
-                                accc = rr.cls ? acc : acc_f;
+                                kc = (int)(rr.kccls & 0x7fffffffu);
+                                accc = (rr.kccls >> 31) ? acc : acc_f;
                             } else {
                                 live = false;
                             }
@@ -311,50 +354,10 @@ __global__ void __launch_bounds__(MT, 1)
                     }
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
-                    {
-                        // One sample: the forward kernel's FP32 position, its
-                        // eight corner weights.  A sample whose cell falls
-                        // outside the rimmed region (FP32 rounding at the
-                        // region's edge; its weights on owned voxels are zero)
-                        // is clamped into it and adds zeros.
-                        const float kf = (float)k;
-                        const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
-                    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
-                    // local corner indices in the rimmed region: [0, R - 2]
-                    int lx = (int)fx - (x0 - 1), ly = (int)fy - (y0 - 1), lz = (int)fz - (z0 - 1);
-                    const bool inr = (unsigned)lx <= (unsigned)(RX - 2) && (unsigned)ly <= (unsigned)(RY - 2) &&
-                                     (unsigned)lz <= (unsigned)(RZ - 2);
-                    lx = min(max(lx, 0), RX - 2);
-                    ly = min(max(ly, 0), RY - 2);
-                    lz = min(max(lz, 0), RZ - 2);
-                    const float yk = inr ? ys : 0.f;
-                    const float wx = x - fx, wy = yy - fy, wz = z - fz;
-                    const float c0 = yk * (1.f - wz), c1 = yk * wz;
-                    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
-                    const float ux = 1.f - wx;
-                    if (F32) {
-                        float *c = reinterpret_cast<float *>(acc) + lz * PP + ly * PX + lx;
-                        atomicAdd(c, b00 * ux);
-                        atomicAdd(c + 1, b00 * wx);
-                        atomicAdd(c + PX, b01 * ux);
-                        atomicAdd(c + PX + 1, b01 * wx);
-                        atomicAdd(c + PP, b10 * ux);
-                        atomicAdd(c + PP + 1, b10 * wx);
-                        atomicAdd(c + PP + PX, b11 * ux);
-                        atomicAdd(c + PP + PX + 1, b11 * wx);
-                    } else {
-                        unsigned int *c = accc + lz * PP + ly * PX + lx;
-                        atomicAdd(c, fixq(b00 * ux));
-                        atomicAdd(c + 1, fixq(b00 * wx));
-                        atomicAdd(c + PX, fixq(b01 * ux));
-                        atomicAdd(c + PX + 1, fixq(b01 * wx));
-                        atomicAdd(c + PP, fixq(b10 * ux));
-                        atomicAdd(c + PP + 1, fixq(b10 * wx));
-                        atomicAdd(c + PP + PX, fixq(b11 * ux));
-                        atomicAdd(c + PP + PX + 1, fixq(b11 * wx));
-                    }
-                    }
-                    ++k;
+                    // two samples per trip (the second adds zeros past the ray's end)
+                    scatter_sample<F32>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
+                    scatter_sample<F32>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
+                    k += 2;
                 }
                 __syncthreads();  // the list is refilled by the next chunk
             }
@@ -375,6 +378,7 @@ __global__ void __launch_bounds__(MT, 1)
                 own[j] += fmaf((float)v, inv_scale, (float)vf * inv_scale_f);
             }
         }
+        // the rim is never read: its sums may wrap, which does no harm
         __syncthreads();
     }
     // owned voxels to the output
