@@ -122,15 +122,24 @@ def make_inputs(case="clinical", seed=1):
     return g, x
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend=None):
+    """Rank, world size and local rank from the launcher's environment; for
+    N > 1 one process per GPU joins a process group (NCCL on GPUs, gloo for
+    host-only runs).  The replicas exchange only the barrier and the maximum
+    of their timings: the work itself has no collective."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -145,9 +154,16 @@ def max_over_ranks(v, world):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(units_per_rank, steps, secs_max, world):
+    """Whole-job throughput of `world` replicas: every rank does
+    `units_per_rank` per step; the job takes the slowest rank's time."""
+    return world * units_per_rank * steps / secs_max
 
 
 # ---------------------------------------------------------------------------
@@ -326,7 +342,7 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     secs = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
-    value = world * units_step * args.steps / secs
+    value = replica_value(units_step, args.steps, secs, world)
 
     # end to end: the same step through the C ABI with pinned host buffers,
     # host<->device copies inside the timed region
@@ -352,7 +368,7 @@ def run_gpu(args):
         step_host()
     torch.cuda.synchronize(dev)
     secs_e2e = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = world * units_step * args.steps / secs_e2e
+    e2e = replica_value(units_step, args.steps, secs_e2e, world)
 
     pk, pk_kind = peaks()
     # dominant kernel: the matched backprojector (largest share of a step)
