@@ -134,6 +134,24 @@ tg_status tg_backproject_noalloc(const tg_geometry *geo, const double *angles, i
 tg_status tg_gradient(const tg_geometry *geo, const double *angles, int nAngles, const float *vol,
                       const float *proj, float *grad, int accumulate, int batch, void *stream);
 
+/* Batches of volumes with different geometries (sizes, angles, detector):
+ * volume v has geometry geos[v] and nAngles[v] angles angles[v] (host
+ * arrays); the volumes are packed back to back in `vol` and their
+ * projection sets back to back in `proj` (device memory, else TG_ERR_ARG).
+ * One launch of the interpolated projector (volume slices of up to 16
+ * volumes and 2048 slices share one texture; larger batches run in chunks)
+ * and one of the matched backprojector per chunk of 16 volumes.
+ *   tg_forward_batched:     proj = A_v vol_v for every v;
+ *   tg_backproject_batched: vol = A_v^T proj_v;
+ *   tg_gradient_batched:    grad (=|+=) A_v^T (A_v vol_v - proj_v), proj may
+ *                           be NULL (then A_v^T A_v vol_v). */
+tg_status tg_forward_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                             const float *vol, float *proj, void *stream);
+tg_status tg_backproject_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                                 const float *proj, float *vol, void *stream);
+tg_status tg_gradient_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                              const float *vol, const float *proj, float *grad, int accumulate, void *stream);
+
 /* FDK (Sec. 2.1, direct methods): cosine pre-weight |(P-S).n|/|P-S|, Ram-Lak
  * row filter sampled at du*DSO/DSD (linear convolution, no wrap-around),
  * TG_FDK_WEIGHT backprojection.  Assumes equally spaced angles over 2 pi.

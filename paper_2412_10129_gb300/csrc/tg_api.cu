@@ -356,6 +356,104 @@ tg_status tg_gradient(const tg_geometry *geo, const double *angles, int nAngles,
     return c.finish();
 }
 
+}  // extern "C"
+
+namespace {
+
+// Ragged batch set-up shared by the *_batched calls: validates every
+// geometry, uploads all angles in one buffer and fills one Grid per volume.
+struct Ragged {
+    std::vector<Grid> grids;
+    std::vector<int> angle0;
+    Angle *dA = nullptr;
+    size_t nvox = 0, nray = 0;
+};
+
+tg_status ragged_setup(Call &c, const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                       Ragged &r) {
+    if (!geos || !angles || !nAngles || nvol < 0) return TG_ERR_ARG;
+    std::vector<Angle> h;
+    for (int v = 0; v < nvol; ++v) {
+        tg_status st = check_common(&geos[v], angles[v], nAngles[v]);
+        if (st != TG_OK) return st;
+        r.angle0.push_back((int)h.size());
+        h.resize(h.size() + (size_t)nAngles[v]);
+        if (nAngles[v] > 0) build_angles(&geos[v], angles[v], nAngles[v], h.data() + r.angle0.back());
+        r.grids.push_back(call_grid(&geos[v], angles[v], nAngles[v]));
+        r.nvox += vol_count(&geos[v]);
+        r.nray += proj_count(&geos[v], nAngles[v]);
+    }
+    if (h.empty()) h.resize(1);
+    r.dA = c.alloc<Angle>(h.size());
+    if (r.dA) c.ok(cudaMemcpyAsync(r.dA, h.data(), h.size() * sizeof(Angle), cudaMemcpyHostToDevice, c.s));
+    return c.status();
+}
+
+bool device_buffer(const void *p) { return p && !is_host(p); }
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_forward_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                             const float *vol, float *proj, void *stream) {
+    if (nvol == 0) return TG_OK;
+    if (!device_buffer(vol) || !device_buffer(proj)) return TG_ERR_ARG;
+    Call c(stream);
+    Ragged r;
+    tg_status st = ragged_setup(c, geos, angles, nAngles, nvol, r);
+    if (st != TG_OK) return c.finish() != TG_OK ? c.status() : st;
+    c.ok(launch_forward_ragged(r.grids.data(), nvol, r.angle0.data(), r.dA, vol, proj, FP_STORE, FpEpilogue{}, c.s));
+    return c.finish();
+}
+
+tg_status tg_backproject_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                                 const float *proj, float *vol, void *stream) {
+    if (nvol == 0) return TG_OK;
+    if (!device_buffer(vol) || !device_buffer(proj)) return TG_ERR_ARG;
+    Call c(stream);
+    Ragged r;
+    tg_status st = ragged_setup(c, geos, angles, nAngles, nvol, r);
+    if (st != TG_OK) return c.finish() != TG_OK ? c.status() : st;
+    unsigned int *amax = c.alloc<unsigned int>(16);
+    if (!c.ok()) return c.finish();
+    std::vector<float> scales;
+    for (const Grid &g : r.grids) scales.push_back(g.delta);
+    BpEpilogue e{};
+    e.absmax = amax;
+    c.ok(launch_backproject_ragged(r.grids.data(), scales.data(), nvol, r.angle0.data(), r.dA, proj, vol, BP_STORE, e,
+                                   c.s));
+    return c.finish();
+}
+
+tg_status tg_gradient_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
+                              const float *vol, const float *proj, float *grad, int accumulate, void *stream) {
+    if (nvol == 0) return TG_OK;
+    if (accumulate != 0 && accumulate != 1) return TG_ERR_ARG;
+    if (!device_buffer(vol) || !device_buffer(grad) || (proj && !device_buffer(proj))) return TG_ERR_ARG;
+    Call c(stream);
+    Ragged r;
+    tg_status st = ragged_setup(c, geos, angles, nAngles, nvol, r);
+    if (st != TG_OK) return c.finish() != TG_OK ? c.status() : st;
+    float *res = c.alloc<float>(r.nray ? r.nray : 1);
+    unsigned int *amax = c.alloc<unsigned int>(16);
+    if (!c.ok()) return c.finish();
+    // r = A x (no data) or r = b - A x, so that A^T (A x - b) = sign * A^T r
+    FpEpilogue fe{};
+    fe.b = proj;
+    c.ok(launch_forward_ragged(r.grids.data(), nvol, r.angle0.data(), r.dA, vol, res, proj ? FP_RESID_W : FP_STORE,
+                               fe, c.s));
+    std::vector<float> scales;
+    for (const Grid &g : r.grids) scales.push_back(proj ? -g.delta : g.delta);
+    BpEpilogue e{};
+    e.lambda = 1.f;
+    e.absmax = amax;
+    if (c.ok())
+        c.ok(launch_backproject_ragged(r.grids.data(), scales.data(), nvol, r.angle0.data(), r.dA, res, grad,
+                                       accumulate ? BP_SIRT : BP_STORE, e, c.s));
+    return c.finish();
+}
+
 tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
                  int filter, void *stream) {
     tg_status st = check_common(geo, angles, nAngles);

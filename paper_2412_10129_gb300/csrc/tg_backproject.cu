@@ -16,8 +16,10 @@
 // accumulated in 32-bit fixed point: y is scaled so that no flush period
 // can overflow (the scale comes from max |y| over the call and a geometric
 // bound on one voxel's summed weights per projection), each product is
-// rounded to an integer with the 1.5 * 2^23 addend, and every FLUSH angles
-// the owned accumulators are converted and added to FP32 registers.
+// rounded to an integer with the 1.5 * 2^23 addend, and after every angle
+// the owned accumulators are converted and added to FP32 registers (a
+// one-angle period keeps the scale as fine as the bound allows; the flush
+// costs about 1 % of the work of an angle).
 // Integer sums do not depend on the order of the atomics, so the result is
 // deterministic; the rounding costs ~1e-6 of max |y| per product, random in
 // sign.  A warp's 32 rays are taken four pixels apart in u and v, so their
@@ -26,6 +28,8 @@
 //
 // TG_FDK_WEIGHT is the FDK backprojection (Sec. 2.1, direct methods):
 //     x_j = (pi / nAngles) sum_a (DSO / L_ja)^2 bilinear(p_a, u_ja, v_ja).
+#include <cstring>
+
 #include "tg_internal.cuh"
 #include "tg_ray.cuh"
 
@@ -98,7 +102,7 @@ constexpr int ACC_WORDS = PP * RZ;                    // one accumulator class
 constexpr float FINE = 64.f;                          // scale ratio of the classes
 constexpr int MT = 512;                               // threads per CTA
 constexpr int OWN = BX * BY * BZ / MT;                // owned voxels per thread
-constexpr int FLUSH = 4;                              // angles per fixed-point period
+constexpr int FLUSH = 1;                              // angles per fixed-point period (flushing costs ~1 %)
 constexpr float MAGIC = 12582912.0f;                  // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;
 static_assert(OWN == 32 && MT == 512 && BX == 32 && BY == 32, "owned-voxel map assumes these sizes");
@@ -109,8 +113,8 @@ __device__ __forceinline__ unsigned int fixq(float a, float b) {
 }
 
 // A ray of the current angle with samples in the brick's region.  Its
-// direction is rebuilt from (iu, iv) when a lane takes it, with the same
-// FP32 expressions as the forward projector.
+// reference point and step are rebuilt from (iu, iv) when a lane takes it,
+// with the forward projector's set-up (ray_frame).
 struct alignas(16) RayRec {
     unsigned int iuv;     // iu | iv << 16
     float ys;             // y, scaled to its fixed-point class
@@ -120,21 +124,6 @@ struct alignas(16) RayRec {
 constexpr int RAYCAP = 1024;  // rays per shared-memory list (a chunk of candidates)
 constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4 + RAYCAP * (int)sizeof(RayRec);
 static_assert(MATCHED_SMEM <= 232448, "shared memory of one CTA");
-
-// Index-space step per sample of ray (iu, iv): the forward kernel's FP32 arithmetic.
-__device__ __forceinline__ void ray_step(const Angle &A, const Grid &g, int iu, int iv, float &gx, float &gy,
-                                         float &gz) {
-    const float fu = (float)iu, fv = (float)iv;
-    const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
-    const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
-    const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
-    const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float invL = rsqrtf(ss);
-    const float f = g.delta * invL;
-    gx = dx * f * g.idx;
-    gy = dy * f * g.idy;
-    gz = dz * f * g.idz;
-}
 
 // Sets up ray (iu, iv) against the region [lo, hi] and fills rec; false
 // when it has no sample there or carries y = 0 (it would add nothing).
@@ -151,19 +140,18 @@ __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const 
         kb0 = r.k0;
         kb1 = r.k1;
     } else {
-        r.sx = A.Sg[0];
-        r.sy = A.Sg[1];
-        r.sz = A.Sg[2];
-        ray_step(A, g, iu, iv, r.gx, r.gy, r.gz);
+        float Ld;
+        ray_frame(A, g, iu, iv, r, Ld);  // the forward kernel's sample positions
     }
     float klo = (float)kb0, khi = (float)kb1;
     const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
     const float lo[3] = {lox, loy, loz}, hi[3] = {hix, hiy, hiz};
+    const float kr = (float)r.kr;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         if (gv[ax] != 0.f) {
             const float ia = 1.f / gv[ax];
-            const float ka = (lo[ax] - sv[ax]) * ia, kc = (hi[ax] - sv[ax]) * ia;
+            const float ka = fmaf(lo[ax] - sv[ax], ia, kr), kc = fmaf(hi[ax] - sv[ax], ia, kr);
             klo = fmaxf(klo, fminf(ka, kc));
             khi = fminf(khi, fmaxf(ka, kc));
         } else if (sv[ax] < lo[ax] || sv[ax] >= hi[ax]) {
@@ -188,7 +176,7 @@ __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const 
 template <bool F32>
 __device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float gx, float gy, float gz, float sx,
                                                float sy, float sz, float ys, int ox, int oy, int oz) {
-    const float kf = (float)k;
+    const float kf = (float)k;  // k relative to the ray's reference sample
     const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
     const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
     const int lx = min(max((int)fx - ox, 0), RX - 2);
@@ -227,14 +215,15 @@ __device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float 
 // precision however small it is -- SIRT and OS-SART divide it by the
 // voxel's column sum -- since fixed point rounds every product to a common
 // absolute step.
+// One brick (bx, by, bz) of one volume: pb are the volume's projections,
+// vb its output (and the SIRT weight's) voxels, gmax its max |y|; the
+// epilogue writes vb directly and adds the FP64 norm to ep.norm[0].
 template <int MODE, bool F32>
-__global__ void __launch_bounds__(MT, 1)
-    k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
-                 BpEpilogue ep, int nbx, int nby) {
+__device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, float *__restrict__ vb,
+                                                 const Angle *__restrict__ angles, const Grid &g, const BpEpilogue &ep,
+                                                 float gmax, int bx, int by, int bz) {
     extern __shared__ unsigned int acc[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int bl = blockIdx.x, b = blockIdx.y;
-    const int bx = bl % nbx, by = (bl / nbx) % nby, bz = bl / (nbx * nby);
     const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
     // region of samples that can touch an owned voxel: p in [o - 1, o + B)
     const float lox = (float)(x0 - 1), loy = (float)(y0 - 1), loz = (float)(z0 - 1);
@@ -247,7 +236,6 @@ __global__ void __launch_bounds__(MT, 1)
     unsigned int *acc_f = acc + ACC_WORDS;
     RayRec *rays = reinterpret_cast<RayRec *>(acc + 2 * ACC_WORDS);
     __shared__ int s_cnt[2];  // rays listed, rays handed out
-    const float gmax = __uint_as_float(ep.absmax[b]);
     const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
     const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
     const float inv_scale = scale > 0.f ? 1.f / scale : 0.f;
@@ -261,7 +249,6 @@ __global__ void __launch_bounds__(MT, 1)
     for (int j = 0; j < OWN; ++j) own[j] = 0.f;
     for (int i = tid; i < 2 * ACC_WORDS; i += MT) acc[i] = 0u;
     __syncthreads();
-    const float *pb = proj + (size_t)b * g.nA * g.nv * g.nu;
     for (int a0 = 0; a0 < g.nA; a0 += FLUSH) {
         const int a1 = min(a0 + FLUSH, g.nA);
         for (int a = a0; a < a1; ++a) {
@@ -325,11 +312,10 @@ __global__ void __launch_bounds__(MT, 1)
                 }
                 __syncthreads();
                 const int nr = s_cnt[0];
-                int k = 1, kc = 0;
-                float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f;
+                int k = 1, kc = 0;  // relative to the current ray's reference sample
+                float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
                 unsigned int *accc = acc;
                 bool live = true;
-                const float sx = A.Sg[0], sy = A.Sg[1], sz = A.Sg[2];
                 while (true) {
                     const bool need = live && k > kc;
                     const unsigned m = __ballot_sync(0xffffffffu, need);
@@ -342,10 +328,18 @@ __global__ void __launch_bounds__(MT, 1)
                             const int idx = base + __popc(m & ((1u << lane) - 1u));
                             if (idx < nr) {
                                 const RayRec rr = rays[idx];
-                                ray_step(A, g, (int)(rr.iuv & 0xffffu), (int)(rr.iuv >> 16), gx, gy, gz);
+                                Ray q;
+                                float Ld;
+                                ray_frame(A, g, (int)(rr.iuv & 0xffffu), (int)(rr.iuv >> 16), q, Ld);
+                                gx = q.gx;
+                                gy = q.gy;
+                                gz = q.gz;
+                                sx = q.sx;
+                                sy = q.sy;
+                                sz = q.sz;
                                 ys = rr.ys;
-                                k = rr.ka;
-                                kc = (int)(rr.kccls & 0x7fffffffu);
+                                k = rr.ka - q.kr;
+                                kc = (int)(rr.kccls & 0x7fffffffu) - q.kr;
                                 accc = (rr.kccls >> 31) ? acc : acc_f;
                             } else {
                                 live = false;
@@ -388,18 +382,78 @@ __global__ void __launch_bounds__(MT, 1)
         const int ix = x0 + lane, iy = y0 + warp + 16 * (j & 1), iz = z0 + (j >> 1);
         const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
         const size_t widx = ok ? ((size_t)iz * g.ny + iy) * g.nx + ix : 0;
-        const size_t vidx = (size_t)b * g.nx * g.ny * g.nz + widx;
         if (MODE == BP_STORE_NORM) {
             const float v = ep.scale * own[j];
             if (ok) {
-                vol[vidx] = v;
+                vb[widx] = v;
                 part += (double)v * (double)v;
             }
         } else {
-            bp_epilogue<MODE>(own[j], ok, vidx, widx, ep, vol, b);
+            bp_epilogue<MODE>(own[j], ok, widx, widx, ep, vb, 0);
         }
     }
-    if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm + b);
+    if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
+}
+
+template <int MODE, bool F32>
+__global__ void __launch_bounds__(MT, 1)
+    k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
+                 BpEpilogue ep, int nbx, int nby) {
+    const int bl = blockIdx.x, b = blockIdx.y;
+    BpEpilogue e = ep;
+    if (e.norm) e.norm += b;
+    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    bp_matched_brick<MODE, F32>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
+                                __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
+}
+
+// Volumes of different sizes and geometries in one launch (packed back to
+// back): blocks blk0[v] .. blk0[v + 1] - 1 are volume v's bricks.
+constexpr int BPR_MAXV = 16;
+struct BpRagged {
+    int nvol;
+    int blk0[BPR_MAXV + 1];
+    int nbx[BPR_MAXV], nby[BPR_MAXV];
+    int a0[BPR_MAXV];
+    long long p0[BPR_MAXV], v0[BPR_MAXV];
+    float scale[BPR_MAXV];
+    Grid g[BPR_MAXV];
+};
+
+template <int MODE, bool F32>
+__global__ void __launch_bounds__(MT, 1)
+    k_bp_matched_ragged(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles,
+                        const __grid_constant__ BpRagged tab, BpEpilogue ep) {
+    const int blk = blockIdx.x;
+    int lo = 0, hi = tab.nvol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab.blk0[mid] <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const int v = lo, bl = blk - tab.blk0[v], nbx = tab.nbx[v], nby = tab.nby[v];
+    BpEpilogue e = ep;
+    e.scale = tab.scale[v];
+    if (e.norm) e.norm += v;
+    bp_matched_brick<MODE, F32>(proj + tab.p0[v], vol + tab.v0[v], angles + tab.a0[v], tab.g[v], e,
+                                __uint_as_float(ep.absmax[v]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
+}
+
+// max |y| of each volume's projections (packed): block row v covers
+// p0[v] .. p0[v] + n[v] - 1.
+struct AbsRagged {
+    long long p0[BPR_MAXV], n[BPR_MAXV];
+};
+__global__ void k_absmax_ragged(const float *__restrict__ y, const __grid_constant__ AbsRagged t, unsigned int *out) {
+    const int v = blockIdx.y;
+    const float *yv = y + t.p0[v];
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < t.n[v];
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(yv[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + v, __float_as_uint(m));
 }
 
 // FDK-weighted backprojection; each thread owns a column of ZC voxels.
@@ -523,6 +577,71 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
     }
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int nvol, const int *angle0,
+                                      const Angle *d_angles, const float *proj, float *vol, int mode,
+                                      const BpEpilogue &ep, cudaStream_t s) {
+    size_t vox = 0, pix = 0;
+    for (int v0 = 0; v0 < nvol; v0 += BPR_MAXV) {
+        const int n = nvol - v0 < BPR_MAXV ? nvol - v0 : BPR_MAXV;
+        BpRagged tab;
+        AbsRagged at;
+        memset(&tab, 0, sizeof(tab));
+        memset(&at, 0, sizeof(at));
+        tab.nvol = n;
+        long long blocks = 0, nmax = 0;
+        size_t cvox = 0, cpix = 0;
+        for (int k = 0; k < n; ++k) {
+            const Grid &g = gs[v0 + k];
+            if (!(g.wbound > 0.f)) return cudaErrorInvalidValue;
+            const int nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY, nbz = (g.nz + BZ - 1) / BZ;
+            tab.g[k] = g;
+            tab.nbx[k] = nbx;
+            tab.nby[k] = nby;
+            tab.a0[k] = angle0[v0 + k];
+            tab.p0[k] = (long long)cpix;
+            tab.v0[k] = (long long)cvox;
+            tab.scale[k] = scales[v0 + k];
+            tab.blk0[k] = (int)blocks;
+            at.p0[k] = (long long)cpix;
+            at.n[k] = (long long)g.nA * g.nv * g.nu;
+            nmax = at.n[k] > nmax ? at.n[k] : nmax;
+            blocks += (long long)nbx * nby * nbz;
+            if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+            cvox += (size_t)g.nx * g.ny * g.nz;
+            cpix += (size_t)at.n[k];
+        }
+        tab.blk0[n] = (int)blocks;
+        cudaError_t e = cudaMemsetAsync(ep.absmax, 0, sizeof(unsigned int) * n, s);
+        if (e != cudaSuccess) return e;
+        if (nmax > 0) {
+            long long nb = (nmax + 255) / 256;
+            if (nb > 152 * 4) nb = 152 * 4;
+            k_absmax_ragged<<<dim3((unsigned)nb, n), 256, 0, s>>>(proj + pix, at, ep.absmax);
+            count_launch();
+        }
+        if (blocks > 0) {
+#define TG_BPR(M, F)                                                                                              \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(k_bp_matched_ragged<M, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                 MATCHED_SMEM);                                                                   \
+        if (e != cudaSuccess) return e;                                                                           \
+        k_bp_matched_ragged<M, F><<<(unsigned)blocks, MT, MATCHED_SMEM, s>>>(proj + pix, vol + vox, d_angles, tab, \
+                                                                            ep);                                 \
+    } while (0)
+            if (mode == BP_STORE) TG_BPR(BP_STORE, false);
+            else if (mode == BP_SIRT) TG_BPR(BP_SIRT, false);
+            else return cudaErrorInvalidValue;
+#undef TG_BPR
+            count_launch();
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        vox += cvox;
+        pix += cpix;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace tg

@@ -7,6 +7,7 @@
 // flight at any time cover one band of rows (one z-slab of the volume) for
 // many angles, which keeps that slab resident in L2 while the angles sweep.
 #include <climits>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) k_fp_interp(const float *__restrict__ vol
     float acc = 0.f;
     for (int k = kw0; k <= kw1; ++k) {
         if (k < k0 || k > k1) continue;
-        const float kf = (float)k;
+        const float kf = (float)(k - r.kr);
         const float x = fmaf(kf, r.gx, r.sx), y = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
         const float fx = floorf(x), fy = floorf(y), fz = floorf(z);
         const float wx = x - fx, wy = y - fy, wz = z - fz;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) k_fp_interp(const float *__restrict__ vol
     }
     const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
     const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
-    fp_epilogue<MODE>(acc * g.delta, valid, pidx, widx, ep, proj, b);
+    fp_epilogue<MODE>(__fmul_rn(acc, g.delta), valid, pidx, widx, ep, proj, b);  // rounded product: no FMA into b - A x
 }
 
 // Four texels of the 2 x 2 footprint around (u, v) in layer `layer` of a
@@ -126,16 +127,21 @@ __device__ __forceinline__ float4 gather4(cudaTextureObject_t t, int layer, floa
 
 // Interpolated projector reading the volume through a layered texture (one
 // layer per z slice): two gathers fetch the eight trilinear corners, the
-// weights stay FP32 software (no hardware filtering).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, float *__restrict__ proj,
-                                                       const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
-                                                       int nvb, int b0) {
-    const int a = blockIdx.y;
-    const int vb = blockIdx.z % nvb, bl = blockIdx.z / nvb, b = b0 + bl;
-    const int lz0 = bl * g.nz;  // first layer of this volume in the array
+// weights stay FP32 software (no hardware filtering).  One ray per thread:
+// block (ub, a, vb) of volume layers lz0 .. lz0 + nz - 1.  PADDED: the
+// array is wider than this volume (ragged batches), so corners past its own
+// nx, ny are zeroed here instead of by the texture border.
+template <int MODE, bool PADDED>
+__device__ __forceinline__ void fp_interp_tex_rays(cudaTextureObject_t tex, float *__restrict__ proj,
+                                                   const Angle *__restrict__ angles, const Grid &g,
+                                                   const FpEpilogue &ep, int ub, int a, int vb, int lz0,
+                                                   size_t pbase, int b) {
     int iu, iv;
-    pixel_of(iu, iv, vb);
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        iu = ub * BU + (warp & 3) * 8 + (lane & 7);
+        iv = vb * BV + (warp >> 2) * 4 + (lane >> 3);
+    }
     const bool valid = iu < g.nu && iv < g.nv;
     const Angle &A = angles[a];
     Ray r;
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, 
     float cfx = -3.0e38f, cfy = 0.f, cfz = 0.f;
     for (int k = kw0; k <= kw1; ++k) {
         if (k < k0 || k > k1) continue;
-        const float kf = (float)k;
+        const float kf = (float)(k - r.kr);
         const float x = fmaf(kf, r.gx, r.sx), y = fmaf(kf, r.gy, r.sy), z = fmaf(kf, r.gz, r.sz);
         const float fx = floorf(x), fy = floorf(y), fz = floorf(z);
         const float wx = x - fx, wy = y - fy, wz = z - fz;
@@ -163,6 +169,10 @@ __global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, 
             const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
             lo = iz >= 0 ? gather4(tex, lz0 + iz, fx + 1.f, fy + 1.f) : zero;
             hi = iz + 1 < nz ? gather4(tex, lz0 + iz + 1, fx + 1.f, fy + 1.f) : zero;
+            if (PADDED) {
+                if ((int)fx + 1 >= g.nx) lo.z = lo.y = hi.z = hi.y = 0.f;  // column i + 1
+                if ((int)fy + 1 >= g.ny) lo.x = lo.y = hi.x = hi.y = 0.f;  // row j + 1
+            }
             cfx = fx;
             cfy = fy;
             cfz = fz;
@@ -173,8 +183,50 @@ __global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, 
         acc += fmaf(wz, c1 - c0, c0);
     }
     const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
-    const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
-    fp_epilogue<MODE>(acc * g.delta, valid, pidx, widx, ep, proj, b);
+    fp_epilogue<MODE>(__fmul_rn(acc, g.delta), valid, pbase + widx, widx, ep, proj, b);  // rounded product: no FMA into b - A x
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, float *__restrict__ proj,
+                                                       const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
+                                                       int nvb, int b0) {
+    const int vb = blockIdx.z % nvb, bl = blockIdx.z / nvb, b = b0 + bl;
+    fp_interp_tex_rays<MODE, false>(tex, proj, angles, g, ep, blockIdx.x, blockIdx.y, vb, bl * g.nz,
+                                    (size_t)b * g.nA * g.nv * g.nu, b);
+}
+
+// Volumes of different sizes and geometries in one launch: volume v's slices
+// are layers lz0[v] .. of one array as wide as the widest volume, its
+// angles start at angles + a0[v], its projections at proj + p0[v]; blocks
+// blk0[v] .. blk0[v + 1] - 1 are its (u-block, angle, row-block) triples.
+constexpr int FPR_MAXV = 16;
+struct FpRagged {
+    int nvol;
+    int blk0[FPR_MAXV + 1];
+    int nub[FPR_MAXV];
+    int lz0[FPR_MAXV];
+    int a0[FPR_MAXV];
+    long long p0[FPR_MAXV];
+    Grid g[FPR_MAXV];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fp_interp_tex_ragged(cudaTextureObject_t tex, float *__restrict__ proj,
+                                                              const Angle *__restrict__ angles,
+                                                              const __grid_constant__ FpRagged tab, FpEpilogue ep) {
+    const int blk = blockIdx.x;
+    int lo = 0, hi = tab.nvol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab.blk0[mid] <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const int v = lo;
+    const Grid &g = tab.g[v];
+    const int local = blk - tab.blk0[v];
+    const int ub = local % tab.nub[v], a = (local / tab.nub[v]) % g.nA, vb = local / (tab.nub[v] * g.nA);
+    fp_interp_tex_rays<MODE, true>(tex, proj, angles + tab.a0[v], g, ep, ub, a, vb, tab.lz0[v],
+                                   (size_t)tab.p0[v], v);
 }
 
 // One layered array (and its texture object) per device and stream, grown
@@ -186,19 +238,20 @@ struct TexCache {
     int nx = 0, ny = 0, nz = 0;
 };
 std::mutex g_tex_mu;
-std::map<std::pair<int, cudaStream_t>, TexCache> g_tex;
+std::map<std::pair<std::pair<int, int>, cudaStream_t>, TexCache> g_tex;  // (device, tag), stream
 
 bool texture_fits(const Grid &g) {
     return g.nx <= 32768 && g.ny <= 32768 && g.nz <= 2048;
 }
 
-cudaError_t texture_for(const Grid &g, cudaStream_t s, TexCache &out) {
+cudaError_t texture_for(const Grid &g, cudaStream_t s, TexCache &out, int tag = 0) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_tex_mu);
-    TexCache &c = g_tex[{dev, s}];
-    if (c.arr && (c.nx != g.nx || c.ny != g.ny || c.nz < g.nz)) {
+    TexCache &c = g_tex[{{dev, tag}, s}];
+    if (c.arr && (c.nx != g.nx || c.ny != g.ny || c.nz < g.nz) && !(tag == 1 && c.nx >= g.nx && c.ny >= g.ny &&
+                                                                      c.nz >= g.nz)) {
         // the old array may still be read by queued kernels of this stream
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
@@ -236,10 +289,11 @@ cudaError_t texture_for(const Grid &g, cudaStream_t s, TexCache &out) {
     return cudaSuccess;
 }
 
-cudaError_t copy_to_texture(const TexCache &c, const float *vol, const Grid &g, cudaStream_t s) {
+cudaError_t copy_to_texture(const TexCache &c, const float *vol, const Grid &g, cudaStream_t s, int layer0 = 0) {
     cudaMemcpy3DParms p = {};
     p.srcPtr = make_cudaPitchedPtr((void *)vol, (size_t)g.nx * sizeof(float), g.nx, g.ny);
     p.dstArray = c.arr;
+    p.dstPos = make_cudaPos(0, 0, layer0);
     p.extent = make_cudaExtent(g.nx, g.ny, g.nz);
     p.kind = cudaMemcpyDeviceToDevice;
     return cudaMemcpy3DAsync(&p, s);
@@ -369,6 +423,72 @@ cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsig
     k_count<<<dim3(nub, g.nA, nvb), 256, 0, s>>>(method, d_angles, g, nvb, out);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_forward_ragged(const Grid *gs, int nvol, const int *angle0, const Angle *d_angles, const float *vol,
+                                  float *proj, int mode, const FpEpilogue &ep, cudaStream_t s) {
+    // chunks of volumes that fit one array (2048 layers) and one table
+    size_t vox = 0, pix = 0;
+    for (int v0 = 0; v0 < nvol;) {
+        FpRagged tab;
+        memset(&tab, 0, sizeof(tab));
+        Grid arr{};
+        int layers = 0, n = 0;
+        long long blocks = 0;
+        size_t cvox = 0, cpix = 0;
+        while (v0 + n < nvol && n < FPR_MAXV && layers + gs[v0 + n].nz <= 2048) {
+            const Grid &g = gs[v0 + n];
+            if (!texture_fits(g)) return cudaErrorInvalidValue;
+            const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
+            tab.g[n] = g;
+            tab.nub[n] = nub;
+            tab.lz0[n] = layers;
+            tab.a0[n] = angle0[v0 + n];
+            tab.p0[n] = (long long)cpix;
+            tab.blk0[n] = (int)blocks;
+            blocks += (long long)nub * g.nA * nvb;
+            if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+            arr.nx = g.nx > arr.nx ? g.nx : arr.nx;
+            arr.ny = g.ny > arr.ny ? g.ny : arr.ny;
+            layers += g.nz;
+            cvox += (size_t)g.nx * g.ny * g.nz;
+            cpix += (size_t)g.nA * g.nu * g.nv;
+            ++n;
+        }
+        if (n == 0) return cudaErrorInvalidValue;  // a single volume of more than 2048 slices
+        tab.nvol = n;
+        tab.blk0[n] = (int)blocks;
+        arr.nz = layers;
+        TexCache tc;
+        cudaError_t e = texture_for(arr, s, tc, 1);
+        if (e != cudaSuccess) return e;
+        size_t off = vox;
+        for (int k = 0; k < n; ++k) {
+            e = copy_to_texture(tc, vol + off, tab.g[k], s, tab.lz0[k]);
+            if (e != cudaSuccess) return e;
+            off += (size_t)tab.g[k].nx * tab.g[k].ny * tab.g[k].nz;
+        }
+        FpEpilogue e1 = ep;
+        if (e1.b) e1.b += pix;
+        if (blocks > 0) {
+            switch (mode) {
+                case FP_STORE:
+                    k_fp_interp_tex_ragged<FP_STORE><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
+                    break;
+                case FP_RESID_W:
+                    k_fp_interp_tex_ragged<FP_RESID_W><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
+                    break;
+                default: return cudaErrorInvalidValue;
+            }
+            count_launch();
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        vox += cvox;
+        pix += cpix;
+        v0 += n;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol, float *proj,

@@ -134,6 +134,12 @@ tg_status validate_geometry(const tg_geometry *g, const double *angles, int nAng
     return TG_OK;
 }
 
+// v = hi + lo with hi = (float)v and lo the rounded remainder.
+static void split(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 tg_status build_angles(const tg_geometry *g, const double *angles, int nAngles, Angle *out) {
     const int nu = g->nDetector[0], nv = g->nDetector[1];
     const double du = g->dDetector[0], dv = g->dDetector[1];
@@ -151,6 +157,10 @@ tg_status build_angles(const tg_geometry *g, const double *angles, int nAngles, 
             A.dir0[i] = (float)(A.P00[i] - f.S[i]);
             A.Uf[i] = (float)A.U[i];
             A.Vf[i] = (float)A.V[i];
+            split(f.S[i] / g->dVoxel[i] + 0.5 * g->nVoxel[i] - 0.5, A.Shi[i], A.Slo[i]);
+            split(A.P00[i] - f.S[i], A.D0hi[i], A.D0lo[i]);
+            split(A.U[i], A.Uhi[i], A.Ulo[i]);
+            split(A.V[i], A.Vhi[i], A.Vlo[i]);
             A.n[i] = (float)f.n[i];
             A.eu[i] = (float)f.eu[i];
             A.ev[i] = (float)f.ev[i];
@@ -241,6 +251,11 @@ Grid make_grid(const tg_geometry *geo, int nAngles) {
     const double acc = geo->accuracy > 0.0 ? geo->accuracy : 0.5;
     g.delta64 = acc * dmin;
     g.delta = (float)g.delta64;
+    for (int i = 0; i < 3; ++i) {
+        const double q = g.delta64 / geo->dVoxel[i];
+        g.sdh[i] = (float)q;
+        g.sdl[i] = (float)(q - (double)g.sdh[i]);
+    }
     g.inv_delta = (float)(1.0 / g.delta64);
     g.du = (float)geo->dDetector[0];
     g.dv = (float)geo->dDetector[1];

@@ -34,6 +34,14 @@ struct alignas(16) Angle {
     float DSO;
     float tau;      // Ram-Lak sampling distance du * DSO / DSD (mm)
     float pad[2];
+    // Double-float (hi + lo) copies for the ray set-up of the interpolated
+    // projector and its transpose: source in index space, P00 - S, U and V
+    // (mm).  They carry ~48 bits, so a ray's reference point near the
+    // volume comes out correctly rounded to FP32.
+    float Shi[3], Slo[3];
+    float D0hi[3], D0lo[3];
+    float Uhi[3], Ulo[3];
+    float Vhi[3], Vlo[3];
 };
 
 // Volume / detector description shared by all kernels of a call.
@@ -53,6 +61,7 @@ struct Grid {
     // Upper bound of the summed trilinear weights one voxel can receive from
     // one projection (matched backprojector fixed-point range).
     float wbound;
+    float sdh[3], sdl[3];  // delta / d per axis, double-float
 };
 
 // Epilogue modes of the forward projector.
@@ -99,9 +108,20 @@ void count_launch(uint64_t n = 1);
 // Kernel launchers (each returns cudaGetLastError()).
 cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol,
                            float *proj, int batch, int mode, const FpEpilogue &ep, cudaStream_t s);
+// Ragged batches (volumes of different geometries, packed back to back):
+// one launch of the interpolated projector; angle0[v] = first Angle of
+// volume v in d_angles.  Modes FP_STORE and FP_RESID_W (W null).
+cudaError_t launch_forward_ragged(const Grid *gs, int nvol, const int *angle0, const Angle *d_angles, const float *vol,
+                                  float *proj, int mode, const FpEpilogue &ep, cudaStream_t s);
 cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles, const float *proj,
                                float *vol, int batch, int mode, const BpEpilogue &ep,
                                cudaStream_t s);
+// Ragged matched backprojection (fixed-point variant): scales[v] is volume
+// v's output multiplier; modes BP_STORE and BP_SIRT (Vw null: accumulate);
+// ep.absmax holds at least min(nvol, 16) words of scratch.
+cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int nvol, const int *angle0,
+                                      const Angle *d_angles, const float *proj, float *vol, int mode,
+                                      const BpEpilogue &ep, cudaStream_t s);
 cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsigned long long *out,
                          cudaStream_t s);
 cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const float *proj, float *out,

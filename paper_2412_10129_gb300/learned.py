@@ -181,12 +181,13 @@ class _LGStep(torch.autograd.Function):
 
 @torch.no_grad()
 def infer_ragged(net: LearnedGradient, geos, bs, x0s, steps: int = 10, etas=None):
-    """The unrolled scheme on volumes of different sizes at once: each
-    step takes every volume's data-fit gradient (one projector pair per
-    geometry), packs all inputs into one buffer, runs each convolution over
-    all volumes in a single launch (the per-volume tile table of
-    tg_conv3d_forward_ragged) and updates all iterates in one launch.
-    Returns the reconstructions (views into one packed FP32 buffer)."""
+    """The unrolled scheme on volumes of different sizes at once: each step
+    takes every volume's data-fit gradient with one launch of each
+    projector for all geometries (tg_gradient_batched), packs all inputs
+    into one buffer, runs each convolution over all volumes in a single
+    launch (the per-volume tile table of tg_conv3d_forward_ragged) and
+    updates all iterates in one launch.  Returns the reconstructions (views
+    into one packed FP32 buffer)."""
     dev = x0s[0].device
     dims = [tuple(g.vol_shape) for g in geos]
     counts = [int(np.prod(d)) for d in dims]
@@ -197,6 +198,7 @@ def infer_ragged(net: LearnedGradient, geos, bs, x0s, steps: int = 10, etas=None
     sx = 1.0 / MU_REF
     x = torch.empty(tot, dtype=torch.float32, device=dev)
     grad = torch.empty(tot, dtype=torch.float32, device=dev)
+    bpk = torch.cat([b.reshape(-1) for b in bs]).contiguous()
     inp = torch.empty((tot, IN_CH), dtype=torch.bfloat16, device=dev)
     ha = torch.empty((tot, 32), dtype=torch.bfloat16, device=dev)
     hb = torch.empty((tot, 32), dtype=torch.bfloat16, device=dev)
@@ -208,8 +210,8 @@ def infer_ragged(net: LearnedGradient, geos, bs, x0s, steps: int = 10, etas=None
     ws = [w.detach().contiguous() for w in net.weights]
     cb = [c.detach().contiguous() for c in net.biases]
     for _ in range(steps):
-        for k, g in enumerate(geos):
-            tg.gradient(g, xs[k], bs[k], out=gs[k])
+        tg.gradient_batched(geos, x, bpk, out=grad)
+        for k in range(len(geos)):
             tg.lg_pack(xs[k], gs[k], IN_CH, sx, sx * etas[k], out=inp[offs[k]:offs[k + 1]])
         h = inp
         for li, (_, _, relu) in enumerate(LAYERS[:-1]):

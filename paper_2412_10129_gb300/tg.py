@@ -87,6 +87,11 @@ def load():
                              ctypes.c_int, _VP],
             "tg_lg_update": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_float, _VP],
             "tg_device_status": [_VP],
+            "tg_forward_batched": [G, ctypes.POINTER(_DP), ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP, _VP],
+            "tg_backproject_batched": [G, ctypes.POINTER(_DP), ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP,
+                                       _VP],
+            "tg_gradient_batched": [G, ctypes.POINTER(_DP), ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP, _VP,
+                                    ctypes.c_int, _VP],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -228,6 +233,60 @@ def gradient(geo, vol, proj=None, out=None, accumulate: bool = False, stream=Non
         out = _empty_like_kind(vol, vol.shape)
     _check("tg_gradient", load().tg_gradient(G.ref, G.ang, G.n, _ptr(vol), None if proj is None else _ptr(proj),
                                              _ptr(out), int(bool(accumulate)), B, _stream(vol, stream)))
+    return out
+
+
+class _Geos:
+    """An array of tg_geometry (and the arrays they point into) for the
+    *_batched calls."""
+
+    def __init__(self, geos):
+        self.items = [_Geo(g) for g in geos]
+        n = len(self.items)
+        self.arr = (_CGeometry * n)(*[it.g for it in self.items])
+        self.angles = (_DP * n)(*[it.ang for it in self.items])
+        self.nang = (ctypes.c_int * n)(*[it.n for it in self.items])
+        self.n = n
+
+
+def _packed_sizes(geos, which):
+    if which == "vol":
+        return [int(np.prod(g.vol_shape)) for g in geos]
+    return [int(np.prod(g.proj_shape)) for g in geos]
+
+
+def forward_batched(geos, vol, out=None, stream=None):
+    """A_v x_v for volumes of different geometries in one launch: ``vol`` is
+    the packed FP32 CUDA buffer of all volumes (back to back), the result the
+    packed projection sets."""
+    G = _Geos(geos)
+    if out is None:
+        out = _torch().empty(sum(_packed_sizes(geos, "proj")), dtype=_torch().float32, device=vol.device)
+    _check("tg_forward_batched", load().tg_forward_batched(G.arr, G.angles, G.nang, G.n, _ptr(vol), _ptr(out),
+                                                           _stream(vol, stream)))
+    return out
+
+
+def backproject_batched(geos, proj, out=None, stream=None):
+    """A_v^T y_v (matched) for volumes of different geometries, packed buffers."""
+    G = _Geos(geos)
+    if out is None:
+        out = _torch().empty(sum(_packed_sizes(geos, "vol")), dtype=_torch().float32, device=proj.device)
+    _check("tg_backproject_batched", load().tg_backproject_batched(G.arr, G.angles, G.nang, G.n, _ptr(proj),
+                                                                   _ptr(out), _stream(proj, stream)))
+    return out
+
+
+def gradient_batched(geos, vol, proj=None, out=None, accumulate: bool = False, stream=None):
+    """A_v^T (A_v x_v - b_v) for volumes of different geometries (packed)."""
+    G = _Geos(geos)
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs out")
+        out = _torch().empty_like(vol)
+    _check("tg_gradient_batched", load().tg_gradient_batched(
+        G.arr, G.angles, G.nang, G.n, _ptr(vol), None if proj is None else _ptr(proj), _ptr(out),
+        int(bool(accumulate)), _stream(vol, stream)))
     return out
 
 
