@@ -121,7 +121,8 @@ struct alignas(16) RayRec {
     int ka;               // samples ka..kc lie in the region (and in the volume)
     unsigned int kccls;   // kc | class << 31 (1: coarse class, 0: fine class)
 };
-constexpr int RAYCAP = 1024;  // rays per shared-memory list (a chunk of candidates)
+constexpr int RAYCAP = 1024;  // rays per shared-memory list
+static_assert(RAYCAP >= 2 * 512, "a chunk takes at least one full step of candidates");
 constexpr int MATCHED_SMEM = 2 * ACC_WORDS * 4 + RAYCAP * (int)sizeof(RayRec);
 static_assert(MATCHED_SMEM <= 232448, "shared memory of one CTA");
 
@@ -284,18 +285,21 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
             // different lengths.
             const int ntu = (u1 - u0 + 32) >> 5, ntv = (v1 - v0 + 16) >> 4;
             const int ncand = ntu * ntv * 16 * 32;
-            for (int c0 = 0; c0 < ncand; c0 += RAYCAP) {
-                const int cend = min(c0 + RAYCAP, ncand);
+            // A chunk scans candidates (one per thread per step) until its
+            // list may not take another step's worth of rays, so phase B
+            // gets 513..RAYCAP rays for its 512 lanes (the last chunk of
+            // an angle may have fewer).
+            for (int c0 = 0; c0 < ncand;) {
                 if (tid == 0) {
                     s_cnt[0] = 0;
                     s_cnt[1] = 0;
                 }
                 __syncthreads();
-                for (int cb = c0 + warp * 32; cb < cend; cb += MT) {  // warp-uniform trips
-                    const int cand = cb + lane;
+                while (c0 < ncand) {
+                    const int cand = c0 + tid;  // warp-uniform step
                     bool keep = false;
                     RayRec rec;
-                    if (cand < cend) {
+                    if (cand < ncand) {
                         const int task = cand >> 5, slot = cand & 31;
                         const int ph = task & 15, tile = task >> 4;
                         const int iu = u0 + (tile % ntu) * 32 + (slot & 7) * 4 + (ph & 3);
@@ -309,8 +313,10 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
                     if (lane == 0 && m) base = atomicAdd(&s_cnt[0], __popc(m));
                     base = __shfl_sync(0xffffffffu, base, 0);
                     if (keep) rays[base + __popc(m & ((1u << lane) - 1u))] = rec;
+                    c0 += MT;
+                    __syncthreads();
+                    if (s_cnt[0] > RAYCAP - MT) break;  // the next step could overflow the list
                 }
-                __syncthreads();
                 const int nr = s_cnt[0];
                 int k = 1, kc = 0;  // relative to the current ray's reference sample
                 float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
