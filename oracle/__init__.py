@@ -17,6 +17,9 @@ follow:
 * ``backproject(method="siddon")`` -- A^T of the Siddon projector.
 * ``fdk_filter``, ``backproject(method="fdk")``, ``fdk`` -- FDK (Sec. 2.1,
   direct methods).
+* ``fdk_variants`` -- FDK filter windows (ram-lak, shepp-logan, cosine,
+  hamming, hann) in the frequency domain, Parker short-scan and Wang
+  displaced-detector weights (Sec. 2.1, direct methods).
 * ``sirt``, ``ossart`` -- Kaczmarz-type methods (Sec. 2.1) with the ordered
   subsets update (Sec. 2.2.2, Eq. 6).
 * ``cgls`` -- CGLS (Sec. 2.1, Krylov methods; Hestenes and Stiefel).
