@@ -368,3 +368,26 @@ def test_training_improves_on_the_untrained_scheme():
     res = np.linalg.norm(oracle.forward(g, x.cpu().numpy()) - b.cpu().numpy().astype(np.float64))
     res0 = np.linalg.norm(oracle.forward(g, x0.cpu().numpy()) - b.cpu().numpy().astype(np.float64))
     assert np.isfinite(res) and res < 2.0 * res0
+
+
+def test_tensor_core_conv_splits_large_batches():
+    """Uniform batches beyond one tensor map's 32 volumes and ragged batches
+    beyond one launch's 16 maps run in several launches with the same
+    results as one volume at a time."""
+    rng = np.random.default_rng(61)
+    w, wo = rand_w(rng, 16, 32)
+    x, xo = bf16_input(rng, (40, 3, 4, 35, 16))
+    y = tg.conv3d(x, w, None, relu=True)
+    for k in (0, 31, 32, 39):
+        assert torch.equal(y[k:k + 1], tg.conv3d(x[k:k + 1].contiguous(), w, None, relu=True))
+    check_bf16_out(y[35:36], oconv.conv3d(xo[35:36], wo, relu=True))
+    dims = [(2 + k % 3, 3, 20 + 7 * k) for k in range(20)]
+    xs = [bf16_input(rng, (1,) + d + (16,))[0] for d in dims]
+    packed = torch.cat([t.reshape(-1, 16) for t in xs]).contiguous()
+    yr = tg.conv3d_ragged(packed, dims, w, None, relu=True)
+    off = 0
+    for t, d in zip(xs, dims):
+        n = int(np.prod(d))
+        assert torch.equal(yr[off:off + n], tg.conv3d(t, w, None, relu=True).reshape(-1, 32))
+        off += n
+    tg.device_status()

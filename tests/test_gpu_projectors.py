@@ -274,3 +274,28 @@ def test_batched_operators_match_per_volume():
         assert rel_l2(bb[vo:vo + nv].cpu().numpy(), oracle.backproject(g, p).ravel()) <= 1e-5
         po += np_
         vo += nv
+
+
+def test_batched_operators_split_into_chunks():
+    """More volumes than one launch's table holds (16) and more slices than
+    one texture array holds (2048): the calls split into chunks and still
+    agree bit for bit with the per-volume operators."""
+    import torch
+    geos = [inputs.circular_geometry((6 + k % 3, 5 + k % 2, 4 + k % 4), (1.0,) * 3, (10, 8), (1.5, 1.5), 3 + k % 2,
+                                     300.0, 500.0) for k in range(18)]
+    geos += [inputs.circular_geometry((3, 3, 1100), (1.0,) * 3, (6, 40), (1.5, 1.5), 2, 2000.0, 3000.0),
+             inputs.circular_geometry((3, 2, 1000), (1.0,) * 3, (6, 40), (1.5, 1.5), 2, 2000.0, 3000.0)]
+    rng = np.random.default_rng(51)
+    vols = [rng.random(g.vol_shape).astype(np.float32) for g in geos]
+    projs = [rng.random(g.proj_shape).astype(np.float32) for g in geos]
+    vpk = torch.from_numpy(np.concatenate([v.ravel() for v in vols])).cuda()
+    ppk = torch.from_numpy(np.concatenate([p.ravel() for p in projs])).cuda()
+    fb = tg.forward_batched(geos, vpk)
+    bb = tg.backproject_batched(geos, ppk)
+    po = vo = 0
+    for g, v, p in zip(geos, vols, projs):
+        vt, pt = torch.from_numpy(v).cuda(), torch.from_numpy(p).cuda()
+        assert torch.equal(fb[po:po + p.size].view(g.proj_shape), tg.forward(g, vt, "interp"))
+        assert torch.equal(bb[vo:vo + v.size].view(g.vol_shape), tg.backproject(g, pt, "matched"))
+        po += p.size
+        vo += v.size
