@@ -70,8 +70,24 @@ enum {
     TG_FDK_WEIGHT = 1  /* voxel-driven (DSO/L)^2 bilinear backprojection times pi/nAngles */
 };
 
-/* FDK filters. */
-enum { TG_RAMLAK = 0 };
+/* FDK row filters (Sec. 2.1 lists FDK "with various filter types"; the
+ * experiments of Sec. 3 use the ramp, Hamming and Shepp-Logan).  Each is the
+ * DFT of the N-periodic discrete ramp kernel (N the smallest power of two
+ * >= max(64, 2 nu)) times a window of f = m/N cycles per sample, f <= 1/2. */
+enum {
+    TG_RAMLAK = 0,      /* W = 1: the spatial ramp kernel itself */
+    TG_SHEPP_LOGAN = 1, /* W = sin(pi f) / (pi f) */
+    TG_COSINE = 2,      /* W = cos(pi f) */
+    TG_HAMMING = 3,     /* W = 0.54 + 0.46 cos(2 pi f) */
+    TG_HANN = 4         /* W = 0.5 + 0.5 cos(2 pi f) */
+};
+
+/* FDK redundancy weights (Sec. 2.1: Parker weights for the angular range,
+ * Wang weights for detector displacement); OR-able flags, not both. */
+enum {
+    TG_FDK_PARKER = 1, /* short scan of increasing first Euler angle over pi + 2 Delta */
+    TG_FDK_WANG = 2    /* full orbit, detector displaced along e_u */
+};
 
 /* OS-SART block order. */
 enum { TG_ORDER_SEQUENTIAL = 0, TG_ORDER_RANDOM = 1 };
@@ -152,12 +168,36 @@ tg_status tg_backproject_batched(const tg_geometry *geos, const double *const *a
 tg_status tg_gradient_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
                               const float *vol, const float *proj, float *grad, int accumulate, void *stream);
 
-/* FDK (Sec. 2.1, direct methods): cosine pre-weight |(P-S).n|/|P-S|, Ram-Lak
- * row filter sampled at du*DSO/DSD (linear convolution, no wrap-around),
- * TG_FDK_WEIGHT backprojection.  Assumes equally spaced angles over 2 pi.
- * vol is overwritten; proj is not modified. */
+/* FDK (Sec. 2.1, direct methods): cosine pre-weight |(P-S).n|/|P-S|, row
+ * filter `filter` (TG_RAMLAK ... TG_HANN) at the isocentre pitch
+ * tau = du*DSO/DSD (linear convolution, no wrap-around), TG_FDK_WEIGHT
+ * backprojection with angle weight pi/nAngles (equally spaced angles over
+ * 2 pi).  vol is overwritten; proj is not modified.  An unknown filter is
+ * TG_ERR_ARG.  Equal to tg_fdk_ex(..., filter, 0, stream). */
 tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
                  float *vol, int filter, void *stream);
+
+/* FDK with redundancy weights `weights` (0, TG_FDK_PARKER or TG_FDK_WANG).
+ *   TG_FDK_PARKER: beta_a = theta_a - theta_0 of the first Euler angle,
+ *     which must increase with a over beta_max = pi + 2 Delta > pi
+ *     (else TG_ERR_GEOMETRY).  A ray of fan angle gamma = atan2((P-S).e_u,
+ *     (D-S).n) is multiplied by Parker's weight with g = -gamma:
+ *     sin^2(pi/4 beta/(Delta - g)) below 2 Delta - 2 g, 1 up to pi - 2 g,
+ *     sin^2(pi/4 (pi + 2 Delta - beta)/(Delta + g)) up to pi + 2 Delta;
+ *     the backprojection's angle weight becomes beta_max / (nAngles - 1).
+ *   TG_FDK_WANG: u = (P-S).e_u; the detector covers [u_lo, u_hi] around
+ *     u = 0 with u0 = min(-u_lo, u_hi) > 0 (else TG_ERR_GEOMETRY) and s the
+ *     sign of the longer side; weight 1 + sin(pi/2 clamp(s u, -u0, u0)/u0).
+ * Both flags together, or other bits, are TG_ERR_UNSUPPORTED / TG_ERR_ARG. */
+tg_status tg_fdk_ex(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                    float *vol, int filter, int weights, void *stream);
+
+/* The pre-weighting and row filtering of tg_fdk_ex alone:
+ * out[a][v][u] = (1/tau_a) sum_j g[|u - j|] w[a][v][j] proj[a][v][j] with the
+ * pre-weight w (cosine times Parker or Wang) and the filter kernel g.
+ * proj and out: [nAngles][nv][nu], distinct buffers. */
+tg_status tg_fdk_filter(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                        float *out, int filter, int weights, void *stream);
 
 /* SIRT (Sec. 2.1): x <- P(x + lambda V A^T W (b - A x)), W = 1/(A 1),
  * V = 1/(A^T 1) (0 where the sum is 0), P = clamp at 0 when nonneg != 0.

@@ -454,11 +454,52 @@ tg_status tg_gradient_batched(const tg_geometry *geos, const double *const *angl
     return c.finish();
 }
 
-tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
-                 int filter, void *stream) {
+// Pre-weighting and row filtering shared by tg_fdk_ex and tg_fdk_filter:
+// uploads the FDK constants, computes the windowed taps and runs the row
+// filter from p into filt (device buffers).
+static void fdk_rows(Call &c, const tg_geometry *geo, const double *angles, int nA, const Angle *dA, const Grid &g,
+                     int filter, int weights, const float *p, float *filt, double *angle_weight) {
+    std::vector<FdkAngle> h((size_t)nA);
+    float Delta = 0.f;
+    tg_status st = build_fdk_angles(geo, angles, nA, weights, h.data(), &Delta, angle_weight);
+    if (st != TG_OK) {
+        c.ok(cudaErrorInvalidValue);
+        return;
+    }
+    FdkAngle *dF = c.alloc<FdkAngle>(h.size());
+    float *taps = nullptr;
+    double *work = nullptr;
+    if (filter != TG_RAMLAK) {
+        taps = c.alloc<float>((size_t)geo->nDetector[0]);
+        work = c.alloc<double>(fdk_taps_scratch(geo->nDetector[0]) / sizeof(double));
+    }
+    if (!c.ok()) return;
+    c.ok(cudaMemcpyAsync(dF, h.data(), h.size() * sizeof(FdkAngle), cudaMemcpyHostToDevice, c.s));
+    if (c.ok() && filter != TG_RAMLAK) c.ok(launch_fdk_taps(geo->nDetector[0], filter, work, taps, c.s));
+    if (c.ok()) c.ok(launch_fdk_filter(g, dA, dF, taps, filter, weights, Delta, p, filt, 1, c.s));
+}
+
+// Host-side checks of the FDK options (before any CUDA call).
+static tg_status check_fdk(const tg_geometry *geo, const double *angles, int nAngles, int filter, int weights) {
+    if (filter < TG_RAMLAK || filter > TG_HANN) return TG_ERR_ARG;
+    if (weights & ~(TG_FDK_PARKER | TG_FDK_WANG)) return TG_ERR_ARG;
+    if (weights == (TG_FDK_PARKER | TG_FDK_WANG)) return TG_ERR_UNSUPPORTED;
+    if (fdk_filter_smem(geo->nDetector[0], filter) > 227 * 1024) return TG_ERR_UNSUPPORTED;
+    if (weights && nAngles > 0) {
+        std::vector<FdkAngle> h((size_t)nAngles);
+        float Delta;
+        double aw;
+        return build_fdk_angles(geo, angles, nAngles, weights, h.data(), &Delta, &aw);
+    }
+    return TG_OK;
+}
+
+tg_status tg_fdk_ex(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                    int filter, int weights, void *stream) {
     tg_status st = check_common(geo, angles, nAngles);
     if (st != TG_OK) return st;
-    if (filter != TG_RAMLAK) return TG_ERR_ARG;
+    st = check_fdk(geo, angles, nAngles, filter, weights);
+    if (st != TG_OK) return st;
     if (!vol || (nAngles > 0 && !proj)) return TG_ERR_ARG;
     const size_t nvox = vol_count(geo), nray = proj_count(geo, nAngles);
     Call c(stream);
@@ -473,11 +514,38 @@ tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, cons
     float *filt = c.alloc<float>(nray);
     if (!c.ok()) return c.finish();
     const Grid g = call_grid(geo, angles, nAngles);
-    c.ok(launch_fdk_filter(g, dA, p.dev, filt, 1, c.s));
+    double aw = 0.0;
+    fdk_rows(c, geo, angles, nAngles, dA, g, filter, weights, p.dev, filt, &aw);
     BpEpilogue e{};
-    e.scale = (float)(M_PI / nAngles);
+    e.scale = (float)aw;
     if (c.ok()) c.ok(launch_backproject(TG_FDK_WEIGHT, g, dA, filt, v.dev, 1, BP_STORE, e, c.s));
     stage_out(c, v);
+    return c.finish();
+}
+
+tg_status tg_fdk(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                 int filter, void *stream) {
+    return tg_fdk_ex(geo, angles, nAngles, proj, vol, filter, 0, stream);
+}
+
+tg_status tg_fdk_filter(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *out,
+                        int filter, int weights, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    st = check_fdk(geo, angles, nAngles, filter, weights);
+    if (st != TG_OK) return st;
+    if (nAngles == 0) return TG_OK;
+    if (!proj || !out || (const void *)proj == (const void *)out) return TG_ERR_ARG;
+    const size_t nray = proj_count(geo, nAngles);
+    Call c(stream);
+    View<const float> p = stage_in(c, proj, nray, true);
+    View<float> o = stage_in(c, out, nray, false);
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    if (!c.ok()) return c.finish();
+    const Grid g = call_grid(geo, angles, nAngles);
+    double aw = 0.0;
+    fdk_rows(c, geo, angles, nAngles, dA, g, filter, weights, p.dev, o.dev, &aw);
+    stage_out(c, o);
     return c.finish();
 }
 
@@ -582,7 +650,10 @@ tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int bat
     switch (op) {
         case 0:
         case 1: f = ang; break;
-        case 2: f = ang + 4 * nray + 16; break;
+        case 2:
+            f = ang + 4 * nray + 16 + sizeof(FdkAngle) * (size_t)(nAngles > 0 ? nAngles : 1) + 16 +
+                4 * (size_t)geo->nDetector[0] + 16 + fdk_taps_scratch(geo->nDetector[0]) + 16;
+            break;
         case 3:
         case 4: {
             const int bs = op == 3 ? (nAngles > 0 ? nAngles : 1) : blocksize;

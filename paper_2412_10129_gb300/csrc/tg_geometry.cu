@@ -181,6 +181,49 @@ tg_status build_angles(const tg_geometry *g, const double *angles, int nAngles, 
     return TG_OK;
 }
 
+tg_status build_fdk_angles(const tg_geometry *g, const double *angles, int nAngles, int weights, FdkAngle *out,
+                           float *Delta, double *angle_weight) {
+    const int nu = g->nDetector[0], nv = g->nDetector[1];
+    const double du = g->dDetector[0], dv = g->dDetector[1];
+    double bmax = 0.0;
+    if (weights & TG_FDK_PARKER) {
+        // a short scan of increasing first Euler angle beyond pi
+        if (nAngles < 2) return TG_ERR_GEOMETRY;
+        for (int a = 1; a < nAngles; ++a)
+            if (!(angles[3 * a] > angles[3 * (a - 1)])) return TG_ERR_GEOMETRY;
+        bmax = angles[3 * (nAngles - 1)] - angles[0];
+        if (!(bmax > M_PI)) return TG_ERR_GEOMETRY;
+        *Delta = (float)(0.5 * (bmax - M_PI));
+        *angle_weight = bmax / (nAngles - 1);
+    } else {
+        *Delta = 0.f;
+        *angle_weight = nAngles > 0 ? M_PI / nAngles : 0.0;
+    }
+    for (int a = 0; a < nAngles; ++a) {
+        Frame f = frame(g, angles, a);
+        FdkAngle &F = out[a];
+        memset(&F, 0, sizeof(F));
+        double DS[3], P00S[3];
+        for (int i = 0; i < 3; ++i) {
+            DS[i] = f.D[i] - f.S[i];
+            P00S[i] = DS[i] + (0.5 - 0.5 * nu) * du * f.eu[i] + (0.5 - 0.5 * nv) * dv * f.ev[i];
+        }
+        F.depth = (float)dot(DS, f.n);
+        F.u00 = (float)dot(P00S, f.eu);
+        F.v00 = (float)dot(P00S, f.ev);
+        F.beta = (float)(angles[3 * a] - angles[0]);
+        if (weights & TG_FDK_WANG) {
+            const double uc = dot(DS, f.eu);
+            const double lo = uc - 0.5 * nu * du, hi = uc + 0.5 * nu * du;
+            const double u0 = -lo < hi ? -lo : hi;
+            if (!(u0 > 0.0)) return TG_ERR_GEOMETRY;
+            F.wu0 = (float)u0;
+            F.wside = hi >= -lo ? 1.f : -1.f;
+        }
+    }
+    return TG_OK;
+}
+
 // A voxel's trilinear support is a cube of side 2 d.  One ray keeps at most
 // 2 sqrt(3) max(d) / delta + 1 samples in it, each with weight <= 1; the
 // rays through it are those whose pixels lie in its shadow, whose diameter

@@ -44,6 +44,18 @@ struct alignas(16) Angle {
     float Vhi[3], Vlo[3];
 };
 
+// Per-projection constants of the FDK pre-weights (mm, FP64-derived):
+// pixel (iu, iv) lies at u = u00 + iu du, v = v00 + iv dv along e_u, e_v
+// from the source's foot point on the detector plane, at distance
+// depth = (D - S).n from the source.
+struct FdkAngle {
+    float depth;
+    float u00, v00;
+    float beta;         // Parker: theta_a - theta_0
+    float wu0, wside;   // Wang: half-width of the doubly seen region, sign of the longer side
+    float pad[2];
+};
+
 // Volume / detector description shared by all kernels of a call.
 struct Grid {
     int nx, ny, nz;
@@ -99,6 +111,11 @@ struct BpEpilogue {
 tg_status build_angles(const tg_geometry *geo, const double *angles, int nAngles, Angle *out);
 tg_status validate_geometry(const tg_geometry *geo, const double *angles, int nAngles);
 Grid make_grid(const tg_geometry *geo, int nAngles);
+// FDK pre-weight constants and the backprojection's angle weight for the
+// weights flags (TG_FDK_PARKER / TG_FDK_WANG); TG_ERR_GEOMETRY when the
+// orbit or detector does not admit them.
+tg_status build_fdk_angles(const tg_geometry *geo, const double *angles, int nAngles, int weights,
+                           FdkAngle *out, float *Delta, double *angle_weight);
 // Fills g.wbound for the given projections (see Grid::wbound).
 void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles, Grid &g);
 
@@ -124,8 +141,16 @@ cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int n
                                       const BpEpilogue &ep, cudaStream_t s);
 cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsigned long long *out,
                          cudaStream_t s);
-cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const float *proj, float *out,
-                              int batch, cudaStream_t s);
+// FDK row filters (tg_fdk.cu).  taps: the windowed kernel g[0..nu) from
+// launch_fdk_taps (unused for TG_RAMLAK, may be null); work: fdk_taps_scratch
+// bytes of device scratch.
+int fdk_fft_length(int nu);
+size_t fdk_taps_scratch(int nu);
+size_t fdk_filter_smem(int nu, int filter);
+cudaError_t launch_fdk_taps(int nu, int filter, double *work, float *taps, cudaStream_t s);
+cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const FdkAngle *d_fa, const float *taps,
+                              int filter, int weights, float Delta, const float *proj, float *out, int batch,
+                              cudaStream_t s);
 
 // Learned-gradient network kernels (tg_conv.cu).
 cudaError_t launch_conv3d(const void *x, const float *w, const float *bias, void *y, int N, int Z, int Y, int X,

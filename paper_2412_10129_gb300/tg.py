@@ -18,7 +18,10 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtg.so")
 
 TG_INTERP, TG_SIDDON = 0, 1
 TG_MATCHED, TG_FDK_WEIGHT = 0, 1
-TG_RAMLAK = 0
+TG_RAMLAK, TG_SHEPP_LOGAN, TG_COSINE, TG_HAMMING, TG_HANN = 0, 1, 2, 3, 4
+FILTERS = {"ram-lak": TG_RAMLAK, "shepp-logan": TG_SHEPP_LOGAN, "cosine": TG_COSINE, "hamming": TG_HAMMING,
+           "hann": TG_HANN}
+TG_FDK_PARKER, TG_FDK_WANG = 1, 2
 TG_ORDER_SEQUENTIAL, TG_ORDER_RANDOM = 0, 1
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "invalid geometry", 3: "device out of memory",
@@ -66,6 +69,8 @@ def load():
             "tg_forward": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
             "tg_backproject": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
             "tg_fdk": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP],
+            "tg_fdk_ex": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
+            "tg_fdk_filter": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
             "tg_sirt": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_float, ctypes.c_int, _DP, _VP],
             "tg_ossart": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_uint64, ctypes.c_float, ctypes.c_int, _DP, _VP],
@@ -290,12 +295,33 @@ def gradient_batched(geos, vol, proj=None, out=None, accumulate: bool = False, s
     return out
 
 
-def fdk(geo, proj, out=None, stream=None):
-    """FDK reconstruction (Ram-Lak)."""
+def _fdk_options(filter, parker, wang):
+    if filter not in FILTERS:
+        raise ValueError(f"unknown filter {filter!r}; one of {sorted(FILTERS)}")
+    return FILTERS[filter], (TG_FDK_PARKER if parker else 0) | (TG_FDK_WANG if wang else 0)
+
+
+def fdk(geo, proj, filter: str = "ram-lak", parker: bool = False, wang: bool = False, out=None, stream=None):
+    """FDK reconstruction (tg_fdk_ex): cosine pre-weight, optional Parker
+    (short scan) or Wang (displaced detector) weights, row filter ``filter``
+    (ram-lak, shepp-logan, cosine, hamming, hann), weighted backprojection."""
     G = _Geo(geo)
+    f, w = _fdk_options(filter, parker, wang)
     if out is None:
         out = _empty_like_kind(proj, geo.vol_shape)
-    _check("tg_fdk", load().tg_fdk(G.ref, G.ang, G.n, _ptr(proj), _ptr(out), TG_RAMLAK, _stream(proj, stream)))
+    _check("tg_fdk_ex", load().tg_fdk_ex(G.ref, G.ang, G.n, _ptr(proj), _ptr(out), f, w, _stream(proj, stream)))
+    return out
+
+
+def fdk_filter(geo, proj, filter: str = "ram-lak", parker: bool = False, wang: bool = False, out=None,
+               stream=None):
+    """The pre-weighted, row-filtered projections of tg_fdk_ex (tg_fdk_filter)."""
+    G = _Geo(geo)
+    f, w = _fdk_options(filter, parker, wang)
+    if out is None:
+        out = _empty_like_kind(proj, geo.proj_shape)
+    _check("tg_fdk_filter", load().tg_fdk_filter(G.ref, G.ang, G.n, _ptr(proj), _ptr(out), f, w,
+                                                 _stream(proj, stream)))
     return out
 
 

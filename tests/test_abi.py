@@ -84,7 +84,10 @@ def test_invalid_arguments_are_rejected(lib):
     assert lib.tg_forward(G.ref, None, 3, None, None, 0, 1, None) == 1
     v = np.zeros(g.vol_shape, np.float32)
     assert lib.tg_backproject(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 5, 1, None) == 1
-    assert lib.tg_fdk(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 3, None) == 1
+    assert lib.tg_fdk(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 5, None) == 1
+    assert lib.tg_fdk(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, -1, None) == 1
+    assert lib.tg_fdk_ex(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 0, 4, None) == 1
+    assert lib.tg_fdk_filter(G.ref, G.ang, G.n, p.ctypes.data, p.ctypes.data, 0, 0, None) == 1
     assert lib.tg_sirt(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, -1, 1.0, 1, None, None) == 1
     assert lib.tg_ossart(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 2, 0, 0, 0, 1.0, 1, None, None) == 1
     assert lib.tg_ossart(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 2, 2, 9, 0, 1.0, 1, None, None) == 1
@@ -109,3 +112,29 @@ def test_workspace_size(lib):
     assert tg.workspace_size(g, "cgls") >= 4 * (2 * nray + 2 * nvox)
     assert tg.workspace_size(g, "ossart", blocksize=20) >= 4 * nvox * 36
     assert tg.workspace_size(g, "forward") < 1 << 20
+
+
+def test_fdk_weight_options_are_checked_on_the_host(lib):
+    """Parker needs increasing angles over more than pi, Wang a detector that
+    reaches across the central ray, and the two are not combined; all are
+    refused before any CUDA call."""
+    import math
+    g = _geo()  # full orbit of 4 angles: 0 .. 3/2 pi
+    G = tg._Geo(g)
+    p = np.zeros(g.proj_shape, np.float32)
+    v = np.zeros(g.vol_shape, np.float32)
+    assert lib.tg_fdk_ex(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 0, 3, None) == 6
+    short = inputs.circular_geometry((8, 8, 8), (1.0,) * 3, (10, 10), (1.5, 1.5), 4, 100.0, 160.0,
+                                     arc=0.9 * math.pi)
+    S = tg._Geo(short)
+    assert lib.tg_fdk_ex(S.ref, S.ang, S.n, p.ctypes.data, v.ctypes.data, 0, 1, None) == 2
+    back = inputs.circular_geometry((8, 8, 8), (1.0,) * 3, (10, 10), (1.5, 1.5), 4, 100.0, 160.0)
+    back.angles[:, 0] = back.angles[::-1, 0]
+    B = tg._Geo(back)
+    assert lib.tg_fdk_filter(B.ref, B.ang, B.n, p.ctypes.data, v.ctypes.data, 0, 1, None) == 2
+    off = _geo()
+    off.offDetector[:, 0] = 9 * 1.5
+    O = tg._Geo(off)
+    assert lib.tg_fdk_ex(O.ref, O.ang, O.n, p.ctypes.data, v.ctypes.data, 0, 2, None) == 2
+    with pytest.raises(ValueError):
+        tg.fdk(g, p, "gaussian")
