@@ -23,6 +23,8 @@ follow:
 * ``sirt``, ``ossart`` -- Kaczmarz-type methods (Sec. 2.1) with the ordered
   subsets update (Sec. 2.2.2, Eq. 6).
 * ``cgls`` -- CGLS (Sec. 2.1, Krylov methods; Hestenes and Stiefel).
+* ``mlem``, ``osem`` -- MLEM (Sec. 2.1, Eq. 5) and its ordered-subsets form
+  (statistical methods; Hudson and Larkin), with either projector pair.
 * ``conv`` -- the 3x3x3 convolutions of the learned-gradient network and
   their transposes (the learned use of the PyTorch wrappers, Sec. 2.8).
 * ``learned`` -- one learned-gradient step x + Gamma(x, A^T(Ax - b)) and its
@@ -328,3 +330,57 @@ def cgls(geo, b, niter: int, x0=None):
         gamma = gamma_new
         hist.append(float(np.linalg.norm(r)))
     return x, np.array(hist)
+
+
+# ---------------------------------------------------------------------------
+# Statistical methods (Sec. 2.1): MLEM (Eq. 5) and OS-EM.
+# ---------------------------------------------------------------------------
+
+_EM_PAIRS = {"interp": ("interp", "matched"), "siddon": ("siddon", "siddon")}
+
+
+def _safe_div(num: np.ndarray, den: np.ndarray) -> np.ndarray:
+    out = np.zeros_like(num)
+    nz = den != 0
+    out[nz] = num[nz] / den[nz]
+    return out
+
+
+def osem(geo, b, niter: int, blocksize: int, x0=None, method: str = "interp"):
+    """OS-EM (Hudson and Larkin 1994): for each block s of consecutive angles
+    in acquisition order,
+        x <- x / (A_s^T 1) * A_s^T (b_s / (A_s x)),
+    the MLEM update of Eq. 5 restricted to the block (Eq. 5's normalisation
+    is the backprojection of ones, the sensitivity of each voxel).  A ray
+    with A_s x = 0 contributes 0; a voxel the block does not see
+    (A_s^T 1 = 0) keeps its value.  x0 = 1 unless given.  ``method``
+    picks the pair (A, A^T): interpolated + matched, or Siddon + its
+    transpose.  Returns (x, ||A x_k - b|| after each iteration)."""
+    fp, bp = _EM_PAIRS[method]
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    b = _f64(b).reshape(geo.proj_shape)
+    x = np.ones((nz, ny, nx)) if x0 is None else _f64(x0).copy()
+    blocks = subsets(geo.nAngles, blocksize)
+    sub = [geo.subset(idx) for idx in blocks]
+    sens = [backproject(g, np.ones(g.proj_shape), bp) for g in sub]
+    hist = []
+    for _ in range(niter):
+        for idx, g, sv in zip(blocks, sub, sens):
+            ratio = _safe_div(b[idx], forward(g, x, fp))
+            x = np.where(sv != 0, x * _safe_inv(sv) * backproject(g, ratio, bp), x)
+        hist.append(float(np.linalg.norm(forward(geo, x, fp) - b)))
+    return x, np.array(hist)
+
+
+def mlem(geo, b, niter: int, x0=None, method: str = "interp"):
+    """MLEM (Eq. 5): OS-EM with one block holding every angle."""
+    return osem(geo, b, niter, max(int(geo.nAngles), 1), x0, method)
+
+
+def poisson_loglik(geo, x, b, method: str = "interp") -> float:
+    """sum_i b_i log (A x)_i - (A x)_i over rays with (A x)_i > 0 (the
+    objective MLEM increases; constant terms dropped)."""
+    y = forward(geo, x, _EM_PAIRS[method][0])
+    b = _f64(b).reshape(y.shape)
+    m = y > 0
+    return float(np.sum(b[m] * np.log(y[m]) - y[m]))
