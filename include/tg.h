@@ -67,7 +67,10 @@ enum {
 /* Backprojectors. */
 enum {
     TG_MATCHED = 0,    /* exact transpose of TG_INTERP (A^T of Eq. 4) */
-    TG_FDK_WEIGHT = 1  /* voxel-driven (DSO/L)^2 bilinear backprojection times pi/nAngles */
+    TG_FDK_WEIGHT = 1, /* voxel-driven (DSO/L)^2 bilinear backprojection times pi/nAngles */
+    TG_SIDDON_BP = 2   /* exact transpose of TG_SIDDON: x_j = sum_i |segment_i & voxel_j| y_i
+                          (FP32 reductions in device memory: the summation order, and so the
+                          last bits, vary between runs) */
 };
 
 /* FDK row filters (Sec. 2.1 lists FDK "with various filter types"; the
@@ -294,8 +297,25 @@ tg_status tg_lg_update(const float *x, const float *net, float *xnext, size_t nv
  * spin without a limit; this is how a caller learns that a limit ran out. */
 tg_status tg_device_status(void *stream);
 
+/* MLEM (Sec. 2.1, Eq. 5; statistical methods): x <- x V A^T (b / (A x)),
+ * V = 1/(A^T 1), the Kullback-Leibler / Poisson-likelihood counterpart of
+ * Eq. 4.  A ray with A x = 0 contributes 0; a voxel with A^T 1 = 0 keeps its
+ * value.  method TG_INTERP uses (TG_INTERP, TG_MATCHED), TG_SIDDON uses
+ * (TG_SIDDON, TG_SIDDON_BP).  vol holds x0 on entry (positive; x0 = 1 is
+ * the usual start) and x on exit.  resid_hist as for tg_sirt. */
+tg_status tg_mlem(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                  float *vol, int niter, int method, double *resid_hist, void *stream);
+
+/* OS-EM (Sec. 2.1; Hudson and Larkin): the MLEM update applied to blocks of
+ * `blocksize` consecutive angles with their own V_s = 1/(A_s^T 1), in the
+ * block order of tg_ossart.  blocksize >= nAngles is MLEM. */
+tg_status tg_osem(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                  float *vol, int niter, int blocksize, int order, uint64_t seed, int method,
+                  double *resid_hist, void *stream);
+
 /* Bytes of device scratch a call would take (op: 0 forward, 1 backproject,
- * 2 fdk, 3 sirt, 4 ossart, 5 cgls; blocksize only for ossart). */
+ * 2 fdk, 3 sirt, 4 ossart, 5 cgls, 6 mlem, 7 osem; blocksize only for
+ * ossart and osem). */
 tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int batch, int blocksize,
                             size_t *bytes);
 

@@ -251,6 +251,100 @@ tg_status sart_family(const tg_geometry *geo, const double *angles, int nA, cons
     return c.finish();
 }
 
+// Shared body of MLEM and OS-EM (MLEM = one block holding every angle):
+// per block s, r = b_s / (A_s x) in the projector's epilogue, then
+// x <- x V_s A_s^T r in the backprojector's epilogue, V_s = 1/(A_s^T 1).
+tg_status em_family(const tg_geometry *geo, const double *angles, int nA, const float *proj, float *vol,
+                    int niter, int blocksize, int order, uint64_t seed, int method, double *resid_hist,
+                    void *stream) {
+    tg_status st = check_common(geo, angles, nA);
+    if (st != TG_OK) return st;
+    if (niter < 0 || blocksize <= 0 || !vol || (nA > 0 && !proj)) return TG_ERR_ARG;
+    if (order != TG_ORDER_SEQUENTIAL && order != TG_ORDER_RANDOM) return TG_ERR_ARG;
+    if (method != TG_INTERP && method != TG_SIDDON) return TG_ERR_ARG;
+    if (niter == 0) return TG_OK;
+    const int bpm = method == TG_INTERP ? TG_MATCHED : TG_SIDDON_BP;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nA);
+    Call c(stream);
+    View<const float> b = stage_in(c, proj, nray, true);
+    View<float> x = stage_in(c, vol, nvox, true);
+    const bool host_hist = resid_hist && is_host(resid_hist);
+    double *hist = resid_hist;
+    if (host_hist) {
+        hist = c.alloc<double>((size_t)niter);
+        c.sync_at_end = true;
+    }
+    if (nA == 0) {  // no data: the iterate does not move
+        if (hist && c.ok()) c.ok(cudaMemsetAsync(hist, 0, sizeof(double) * niter, c.s));
+        stage_out(c, x);
+        if (host_hist && c.ok())
+            c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+        return c.finish();
+    }
+    Angle *dA = upload_angles(c, geo, angles, nA);
+    const Grid g = call_grid(geo, angles, nA);
+    const auto blocks = make_blocks(nA, blocksize);
+    float *r = c.alloc<float>(nray);
+    float *ones = c.alloc<float>(nray);
+    float *V = c.alloc<float>(nvox * blocks.size());
+    float *bacc = bpm == TG_SIDDON_BP ? c.alloc<float>(nvox) : nullptr;
+    double *acc = c.alloc<double>(1);
+    unsigned int *amax = c.alloc<unsigned int>(1);
+    if (!c.ok()) return c.finish();
+    const float scale = bpm == TG_MATCHED ? g.delta : 1.f;
+    c.ok(launch_fill(ones, 1.f, nray, c.s));
+    for (size_t k = 0; k < blocks.size() && c.ok(); ++k) {
+        Grid gs = g;
+        gs.nA = blocks[k].size;
+        BpEpilogue e{};
+        e.scale = scale;
+        e.absmax = amax;
+        e.fp32_acc = 1;
+        c.ok(launch_backproject(bpm, gs, dA + blocks[k].start, ones, V + k * nvox, 1, BP_STORE, e, c.s));
+        c.ok(launch_safe_inverse(V + k * nvox, nvox, c.s));
+    }
+    const size_t plane = (size_t)g.nu * g.nv;
+    uint64_t rng = seed;
+    std::vector<int> perm(blocks.size());
+    for (int it = 0; it < niter && c.ok(); ++it) {
+        for (size_t k = 0; k < perm.size(); ++k) perm[k] = (int)k;
+        if (order == TG_ORDER_RANDOM)
+            for (size_t k = perm.size(); k > 1; --k) {
+                const size_t j = (size_t)(splitmix64(rng) % k);
+                int t = perm[k - 1];
+                perm[k - 1] = perm[j];
+                perm[j] = t;
+            }
+        for (size_t q = 0; q < perm.size() && c.ok(); ++q) {
+            const Block &B = blocks[perm[q]];
+            Grid gs = g;
+            gs.nA = B.size;
+            FpEpilogue fe{};
+            fe.b = b.dev + (size_t)B.start * plane;
+            c.ok(launch_forward(method, gs, dA + B.start, x.dev, r, 1, FP_RATIO, fe, c.s));
+            BpEpilogue be{};
+            be.Vw = V + (size_t)perm[q] * nvox;
+            be.scale = scale;
+            be.absmax = amax;
+            be.fp32_acc = 1;
+            be.acc = bacc;
+            c.ok(launch_backproject(bpm, gs, dA + B.start, r, x.dev, 1, BP_MLEM, be, c.s));
+        }
+        if (hist && c.ok()) {
+            c.ok(cudaMemsetAsync(acc, 0, sizeof(double), c.s));
+            FpEpilogue fe{};
+            fe.b = b.dev;
+            fe.norm = acc;
+            c.ok(launch_forward(method, g, dA, x.dev, r, 1, FP_RESID_NORM, fe, c.s));
+            c.ok(launch_sqrt_copy(acc, hist + it, c.s));
+        }
+    }
+    stage_out(c, x);
+    if (host_hist && c.ok())
+        c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+    return c.finish();
+}
+
 }  // namespace
 }  // namespace tg
 
@@ -296,7 +390,7 @@ tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngl
                          float *vol, int method, int batch, void *stream) {
     tg_status st = check_common(geo, angles, nAngles);
     if (st != TG_OK) return st;
-    if (method != TG_MATCHED && method != TG_FDK_WEIGHT) return TG_ERR_ARG;
+    if (method != TG_MATCHED && method != TG_FDK_WEIGHT && method != TG_SIDDON_BP) return TG_ERR_ARG;
     if (batch < 0) return TG_ERR_ARG;
     if (batch == 0) return TG_OK;
     if (!vol || (nAngles > 0 && !proj)) return TG_ERR_ARG;
@@ -314,7 +408,7 @@ tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngl
     if (!c.ok()) return c.finish();
     const Grid g = call_grid(geo, angles, nAngles);
     BpEpilogue e{};
-    e.scale = method == TG_MATCHED ? g.delta : (float)(M_PI / nAngles);
+    e.scale = method == TG_MATCHED ? g.delta : method == TG_SIDDON_BP ? 1.f : (float)(M_PI / nAngles);
     e.absmax = amax;
     c.ok(launch_backproject(method, g, dA, p.dev, v.dev, batch, BP_STORE, e, c.s));
     stage_out(c, v);
@@ -562,6 +656,18 @@ tg_status tg_ossart(const tg_geometry *geo, const double *angles, int nAngles, c
                        resid_hist, stream);
 }
 
+tg_status tg_mlem(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                  int niter, int method, double *resid_hist, void *stream) {
+    return em_family(geo, angles, nAngles, proj, vol, niter, nAngles > 0 ? nAngles : 1, TG_ORDER_SEQUENTIAL, 0,
+                     method, resid_hist, stream);
+}
+
+tg_status tg_osem(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                  int niter, int blocksize, int order, uint64_t seed, int method, double *resid_hist,
+                  void *stream) {
+    return em_family(geo, angles, nAngles, proj, vol, niter, blocksize, order, seed, method, resid_hist, stream);
+}
+
 tg_status tg_cgls(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
                   int niter, double *resid_hist, void *stream) {
     tg_status st = check_common(geo, angles, nAngles);
@@ -663,6 +769,14 @@ tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int bat
             break;
         }
         case 5: f = ang + 4 * (2 * nray + 2 * nvox) + 64; break;
+        case 6:
+        case 7: {
+            const int bs = op == 6 ? (nAngles > 0 ? nAngles : 1) : blocksize;
+            if (bs <= 0) return TG_ERR_ARG;
+            const size_t nb = (size_t)((nAngles + bs - 1) / bs);
+            f = ang + 4 * (2 * nray + nvox * nb + nvox) + 96;
+            break;
+        }
         default: return TG_ERR_ARG;
     }
     *bytes = f;

@@ -66,11 +66,33 @@ __device__ __forceinline__ void bp_epilogue(float sum, bool valid, size_t vidx, 
             if (ep.nonneg) x = fmaxf(x, 0.f);
             vol[vidx] = x;
         }
+    } else if (MODE == BP_MLEM) {
+        if (valid) {
+            const float v = ep.Vw ? ep.Vw[widx] : 1.f;
+            if (v > 0.f) vol[vidx] = vol[vidx] * v * (ep.scale * sum);
+        }
     } else {  // BP_STORE_NORM
         const float s = ep.scale * sum;
         if (valid) vol[vidx] = s;
         const double d = valid ? (double)s : 0.0;
         block_add_bp(d * d, ep.norm + b);
+    }
+}
+
+// The epilogue of a scatter backprojection (Siddon transpose): acc holds
+// A^T y per voxel; one thread per voxel applies the mode.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bp_apply(const float *__restrict__ acc, float *__restrict__ vol, size_t n,
+                                                  BpEpilogue ep) {
+    const int b = blockIdx.y;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    // every thread runs the same number of rounds (BP_STORE_NORM reduces per block)
+    const size_t rounds = (n + stride - 1) / stride;
+    for (size_t r = 0; r < rounds; ++r) {
+        const size_t i = r * stride + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const bool ok = i < n;
+        const size_t vidx = (size_t)b * n + (ok ? i : 0);
+        bp_epilogue<MODE>(ok ? acc[vidx] : 0.f, ok, vidx, ok ? i : 0, ep, vol, b);
     }
 }
 
@@ -565,6 +587,10 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
                 e = f32 ? launch_matched<BP_STORE_NORM, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
                         : launch_matched<BP_STORE_NORM, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
                 break;
+            case BP_MLEM:
+                // a per-voxel multiplicative update: FP32 accumulation
+                e = launch_matched<BP_MLEM, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+                break;
             default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
@@ -576,6 +602,29 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
             case BP_STORE: k_bp_fdk<BP_STORE><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
             case BP_SIRT: k_bp_fdk<BP_SIRT><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
             case BP_STORE_NORM: k_bp_fdk<BP_STORE_NORM><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else if (method == TG_SIDDON_BP) {
+        const size_t n = (size_t)g.nx * g.ny * g.nz;  // per batch item
+        if (batch > 65535) return cudaErrorInvalidConfiguration;
+        if (mode == BP_STORE) {
+            cudaError_t e = cudaMemsetAsync(vol, 0, n * batch * sizeof(float), s);
+            if (e != cudaSuccess) return e;
+            return launch_siddon_scatter(g, d_angles, proj, vol, batch, ep.scale, s);
+        }
+        if (!ep.acc) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(ep.acc, 0, n * batch * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        e = launch_siddon_scatter(g, d_angles, proj, ep.acc, batch, 1.f, s);
+        if (e != cudaSuccess) return e;
+        size_t nb = (n + 255) / 256;
+        if (nb > 152 * 16) nb = 152 * 16;
+        if (nb == 0) nb = 1;
+        dim3 grid((unsigned)nb, batch);
+        switch (mode) {
+            case BP_SIRT: k_bp_apply<BP_SIRT><<<grid, 256, 0, s>>>(ep.acc, vol, n, ep); break;
+            case BP_STORE_NORM: k_bp_apply<BP_STORE_NORM><<<grid, 256, 0, s>>>(ep.acc, vol, n, ep); break;
+            case BP_MLEM: k_bp_apply<BP_MLEM><<<grid, 256, 0, s>>>(ep.acc, vol, n, ep); break;
             default: return cudaErrorInvalidValue;
         }
     } else {

@@ -54,6 +54,8 @@ __device__ __forceinline__ void fp_epilogue(float sum, bool valid, size_t pidx, 
         if (valid) proj[pidx] = sum;
         const double d = valid ? (double)sum : 0.0;
         block_add(d * d, ep.norm + b);
+    } else if (MODE == FP_RATIO) {
+        if (valid) proj[pidx] = sum != 0.f ? ep.b[pidx] / sum : 0.f;
     } else {  // FP_RESID_NORM
         const double d = valid ? (double)sum - (double)ep.b[pidx] : 0.0;
         block_add(d * d, ep.norm + b);
@@ -303,12 +305,11 @@ cudaError_t copy_to_texture(const TexCache &c, const float *vol, const Grid &g, 
 // over the cells the segment crosses.  Parameters are measured in mm from
 // the box entry point, so they stay small and keep FP32 resolution; each
 // crossing parameter is recomputed from its count with one FMA instead of
-// accumulated.
-// With COUNT the walk returns the number of cell segments it visits instead
-// of the line integral (the unit of work the benchmark reports).
-template <bool COUNT = false>
-__device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const Angle &A, const Grid &g,
-                                            int iu, int iv) {
+// accumulated.  The walk calls visit(cell index, segment length) for every
+// cell segment inside the volume: the projector sums length * x, its
+// transpose scatters length * y, the counter counts.
+template <class Visit>
+__device__ __forceinline__ void siddon_walk(const Angle &A, const Grid &g, int iu, int iv, Visit &visit) {
     const float fu = (float)iu, fv = (float)iv;
     const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
     const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
@@ -332,7 +333,7 @@ __device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const A
             tout = -1.f;
         }
     }
-    if (!(tout > tin)) return 0.f;
+    if (!(tout > tin)) return;
     int c[3], st[3];
     float t0[3], dt[3];
 #pragma unroll
@@ -358,13 +359,13 @@ __device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const A
     const float tend = tout - tin;
     int m[3] = {0, 0, 0};
     float tn[3] = {t0[0], t0[1], t0[2]};
-    float tcur = 0.f, acc = 0.f;
+    float tcur = 0.f;
     const int nxy = g.nx * g.ny;
     const int cap = g.nx + g.ny + g.nz + 4;
     for (int it = 0; it < cap && tcur < tend; ++it) {
         const float tnext = fminf(fminf(fminf(tn[0], tn[1]), tn[2]), tend);
         if (c[0] >= 0 && c[0] < g.nx && c[1] >= 0 && c[1] < g.ny && c[2] >= 0 && c[2] < g.nz)
-            acc = COUNT ? acc + 1.f : fmaf(tnext - tcur, __ldg(v + c[2] * nxy + c[1] * g.nx + c[0]), acc);
+            visit(c[2] * nxy + c[1] * g.nx + c[0], tnext - tcur);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             if (tn[a] == tnext) {
@@ -374,7 +375,36 @@ __device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const A
             }
         tcur = tnext;
     }
-    return acc;
+}
+
+struct SiddonSum {
+    const float *__restrict__ v;
+    float acc;
+    __device__ __forceinline__ void operator()(int idx, float len) { acc = fmaf(len, __ldg(v + idx), acc); }
+};
+struct SiddonCount {
+    float acc;
+    __device__ __forceinline__ void operator()(int, float) { acc += 1.f; }
+};
+struct SiddonScatter {
+    float *__restrict__ out;
+    float y;
+    __device__ __forceinline__ void operator()(int idx, float len) { atomicAdd(out + idx, len * y); }
+};
+
+// With COUNT the walk returns the number of cell segments it visits instead
+// of the line integral (the unit of work the benchmark reports).
+template <bool COUNT = false>
+__device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const Angle &A, const Grid &g,
+                                            int iu, int iv) {
+    if (COUNT) {
+        SiddonCount c{0.f};
+        siddon_walk(A, g, iu, iv, c);
+        return c.acc;
+    }
+    SiddonSum f{v, 0.f};
+    siddon_walk(A, g, iu, iv, f);
+    return f.acc;
 }
 
 template <int MODE>
@@ -391,6 +421,24 @@ __global__ void __launch_bounds__(256) k_fp_siddon(const float *__restrict__ vol
     const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
     const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
     fp_epilogue<MODE>(sum, valid, pidx, widx, ep, proj, b);
+}
+
+// Transpose of the Siddon projector: out_j += sum_i |segment_i & cell_j| *
+// scale * y_i.  One thread per ray walks the same cells with the same
+// lengths as the projector and adds each contribution to global memory
+// (FP32 reductions in L2, so the summation order varies between runs).
+__global__ void __launch_bounds__(256) k_bp_siddon_scatter(const float *__restrict__ proj, float *__restrict__ out,
+                                                           const Angle *__restrict__ angles, Grid g, float scale,
+                                                           int nvb) {
+    const int a = blockIdx.y;
+    const int vb = blockIdx.z % nvb, b = blockIdx.z / nvb;
+    int iu, iv;
+    pixel_of(iu, iv, vb);
+    if (iu >= g.nu || iv >= g.nv) return;
+    const float y = scale * proj[(((size_t)b * g.nA + a) * g.nv + iv) * g.nu + iu];
+    if (y == 0.f) return;
+    SiddonScatter f{out + (size_t)b * g.nx * g.ny * g.nz, y};
+    siddon_walk(angles[a], g, iu, iv, f);
 }
 
 // Units of work of a forward projection: kept samples per ray (TG_INTERP)
@@ -491,6 +539,16 @@ cudaError_t launch_forward_ragged(const Grid *gs, int nvol, const int *angle0, c
     return cudaSuccess;
 }
 
+cudaError_t launch_siddon_scatter(const Grid &g, const Angle *d_angles, const float *proj, float *out, int batch,
+                                  float scale, cudaStream_t s) {
+    if (g.nA == 0 || batch == 0) return cudaSuccess;
+    const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
+    if ((long long)nvb * batch > 65535 || g.nA > 65535) return cudaErrorInvalidConfiguration;
+    k_bp_siddon_scatter<<<dim3(nub, g.nA, nvb * batch), 256, 0, s>>>(proj, out, d_angles, g, scale, nvb);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol, float *proj,
                            int batch, int mode, const FpEpilogue &ep, cudaStream_t s) {
     if (g.nA == 0 || batch == 0) return cudaSuccess;
@@ -521,6 +579,7 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
                 case FP_RESID_W: k_fp_interp_tex<FP_RESID_W><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
                 case FP_STORE_NORM: k_fp_interp_tex<FP_STORE_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
                 case FP_RESID_NORM: k_fp_interp_tex<FP_RESID_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_RATIO: k_fp_interp_tex<FP_RATIO><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
                 default: return cudaErrorInvalidValue;
             }
             count_launch();
@@ -535,6 +594,7 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
             case FP_RESID_W: k_fp_interp<FP_RESID_W><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             case FP_STORE_NORM: k_fp_interp<FP_STORE_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             case FP_RESID_NORM: k_fp_interp<FP_RESID_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RATIO: k_fp_interp<FP_RATIO><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             default: return cudaErrorInvalidValue;
         }
     } else if (method == TG_SIDDON) {
@@ -543,6 +603,7 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
             case FP_RESID_W: k_fp_siddon<FP_RESID_W><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             case FP_STORE_NORM: k_fp_siddon<FP_STORE_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             case FP_RESID_NORM: k_fp_siddon<FP_RESID_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RATIO: k_fp_siddon<FP_RATIO><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             default: return cudaErrorInvalidValue;
         }
     } else {

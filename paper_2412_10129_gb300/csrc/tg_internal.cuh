@@ -81,14 +81,16 @@ enum FpMode {
     FP_STORE = 0,     // proj = A x
     FP_RESID_W = 1,   // proj = W (b - A x)               (SIRT / OS-SART)
     FP_STORE_NORM = 2,// proj = A x, norm += ||A x||^2     (CGLS q = A p)
-    FP_RESID_NORM = 3 // norm += ||A x - b||^2, no store   (residual history)
+    FP_RESID_NORM = 3,// norm += ||A x - b||^2, no store   (residual history)
+    FP_RATIO = 4      // proj = b / (A x), 0 where A x = 0  (MLEM / OS-EM)
 };
 
 // Epilogue modes of the backprojectors.
 enum BpMode {
     BP_STORE = 0,      // vol = scale * A^T y
     BP_SIRT = 1,       // vol = clamp(vol + lambda V A^T y)
-    BP_STORE_NORM = 2  // vol = A^T y, norm += ||A^T y||^2 (CGLS s = A^T r)
+    BP_STORE_NORM = 2, // vol = A^T y, norm += ||A^T y||^2 (CGLS s = A^T r)
+    BP_MLEM = 3        // vol = vol V A^T y where V > 0, vol unchanged where V = 0 (MLEM / OS-EM)
 };
 
 struct FpEpilogue {
@@ -105,6 +107,7 @@ struct BpEpilogue {
     double *norm;        // FP64 accumulator (one per batch item)
     unsigned int *absmax;  // device scratch words (TG_MATCHED: max |y| per batch item)
     int fp32_acc;          // TG_MATCHED: accumulate in FP32 (per-voxel relative precision)
+    float *acc;            // TG_SIDDON_BP, modes other than BP_STORE: device scratch of the volume's size
 };
 
 // Host helpers (tg_geometry.cu).
@@ -139,6 +142,9 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
 cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int nvol, const int *angle0,
                                       const Angle *d_angles, const float *proj, float *vol, int mode,
                                       const BpEpilogue &ep, cudaStream_t s);
+// Transpose of the Siddon projector, added into out (tg_forward.cu).
+cudaError_t launch_siddon_scatter(const Grid &g, const Angle *d_angles, const float *proj, float *out, int batch,
+                                  float scale, cudaStream_t s);
 cudaError_t launch_count(int method, const Grid &g, const Angle *d_angles, unsigned long long *out,
                          cudaStream_t s);
 // FDK row filters (tg_fdk.cu).  taps: the windowed kernel g[0..nu) from

@@ -70,7 +70,7 @@ extern "C" tg_status tg_backproject_noalloc(const tg_geometry *geo, const double
     if (!geo) return TG_ERR_ARG;
     tg_status st = validate_geometry(geo, angles, nAngles);
     if (st != TG_OK) return st;
-    if (method != TG_MATCHED && method != TG_FDK_WEIGHT) return TG_ERR_ARG;
+    if (method != TG_MATCHED && method != TG_FDK_WEIGHT && method != TG_SIDDON_BP) return TG_ERR_ARG;
     if (batch < 0) return TG_ERR_ARG;
     if (batch == 0) return TG_OK;
     if (nAngles > NOALLOC_MAX_ANGLES || batch > NOALLOC_MAX_BATCH) return TG_ERR_UNSUPPORTED;
@@ -107,7 +107,7 @@ extern "C" tg_status tg_backproject_noalloc(const tg_geometry *geo, const double
     Grid g = make_grid(geo, nAngles);
     set_weight_bound(geo, angles, nAngles, g);
     BpEpilogue ep{};
-    ep.scale = method == TG_MATCHED ? g.delta : (float)(M_PI / nAngles);
+    ep.scale = method == TG_MATCHED ? g.delta : method == TG_SIDDON_BP ? 1.f : (float)(M_PI / nAngles);
     ep.absmax = amax;  // zeroed by the launcher before use
     e = launch_backproject(method, g, dA, proj, vol, batch, BP_STORE, ep, s);
     if (e == cudaErrorMemoryAllocation) return TG_ERR_OOM;

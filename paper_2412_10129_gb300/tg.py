@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libtg.so")
 
 TG_INTERP, TG_SIDDON = 0, 1
-TG_MATCHED, TG_FDK_WEIGHT = 0, 1
+TG_MATCHED, TG_FDK_WEIGHT, TG_SIDDON_BP = 0, 1, 2
 TG_RAMLAK, TG_SHEPP_LOGAN, TG_COSINE, TG_HAMMING, TG_HANN = 0, 1, 2, 3, 4
 FILTERS = {"ram-lak": TG_RAMLAK, "shepp-logan": TG_SHEPP_LOGAN, "cosine": TG_COSINE, "hamming": TG_HAMMING,
            "hann": TG_HANN}
@@ -75,6 +75,9 @@ def load():
             "tg_ossart": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_uint64, ctypes.c_float, ctypes.c_int, _DP, _VP],
             "tg_cgls": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
+            "tg_mlem": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _DP, _VP],
+            "tg_osem": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                        ctypes.c_int, _DP, _VP],
             "tg_workspace_size": [G, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_size_t)],
             "tg_count_samples": [G, _DP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _VP],
@@ -185,7 +188,7 @@ def _batch(x, base_ndim):
 
 
 _METHOD_FP = {"interp": TG_INTERP, "siddon": TG_SIDDON}
-_METHOD_BP = {"matched": TG_MATCHED, "fdk": TG_FDK_WEIGHT}
+_METHOD_BP = {"matched": TG_MATCHED, "fdk": TG_FDK_WEIGHT, "siddon": TG_SIDDON_BP}
 
 
 def forward(geo, vol, method: str = "interp", out=None, stream=None):
@@ -201,7 +204,8 @@ def forward(geo, vol, method: str = "interp", out=None, stream=None):
 
 
 def backproject(geo, proj, method: str = "matched", out=None, stream=None):
-    """A^T y (matched) or the FDK backprojection: proj [(B,) nA, nv, nu] -> vol."""
+    """A^T y (matched: transpose of the interpolated projector; siddon: of
+    the Siddon projector) or the FDK backprojection: proj [(B,) nA, nv, nu] -> vol."""
     G = _Geo(geo)
     B, batched = _batch(proj, 3)
     shape = ((B,) if batched else ()) + tuple(geo.vol_shape)
@@ -380,8 +384,43 @@ def cgls(geo, proj, niter: int, x0=None, resid: bool = False, stream=None):
     return x
 
 
+def _ones_like_vol(geo, proj):
+    if isinstance(proj, np.ndarray):
+        return np.ones(geo.vol_shape, np.float32)
+    return _torch().ones(geo.vol_shape, dtype=_torch().float32, device=proj.device)
+
+
+def mlem(geo, proj, niter: int, x0=None, method: str = "interp", resid: bool = False, stream=None):
+    """MLEM (Eq. 5) with the (interp, matched) or (siddon, siddon transpose)
+    pair; x0 = 1 unless given.  Returns x (and the residual history)."""
+    G = _Geo(geo)
+    x = x0 if x0 is not None else _ones_like_vol(geo, proj)
+    h, hp = _hist(niter, resid)
+    _check("tg_mlem", load().tg_mlem(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), int(niter), _METHOD_FP[method], hp,
+                                     _stream(proj, stream)))
+    if resid:
+        _sync(proj)
+        return x, h[:niter]
+    return x
+
+
+def osem(geo, proj, niter: int, blocksize: int = 20, order: str = "sequential", seed: int = 0, x0=None,
+         method: str = "interp", resid: bool = False, stream=None):
+    """OS-EM: MLEM updates over blocks of consecutive angles."""
+    G = _Geo(geo)
+    x = x0 if x0 is not None else _ones_like_vol(geo, proj)
+    h, hp = _hist(niter, resid)
+    o = {"sequential": TG_ORDER_SEQUENTIAL, "random": TG_ORDER_RANDOM}[order]
+    _check("tg_osem", load().tg_osem(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), int(niter), int(blocksize), o,
+                                     int(seed), _METHOD_FP[method], hp, _stream(proj, stream)))
+    if resid:
+        _sync(proj)
+        return x, h[:niter]
+    return x
+
+
 def workspace_size(geo, op: str, batch: int = 1, blocksize: int = 20) -> int:
-    ops = {"forward": 0, "backproject": 1, "fdk": 2, "sirt": 3, "ossart": 4, "cgls": 5}
+    ops = {"forward": 0, "backproject": 1, "fdk": 2, "sirt": 3, "ossart": 4, "cgls": 5, "mlem": 6, "osem": 7}
     G = _Geo(geo)
     out = ctypes.c_size_t(0)
     _check("tg_workspace_size", load().tg_workspace_size(G.ref, G.n, ops[op], int(batch), int(blocksize),
