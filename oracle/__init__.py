@@ -23,6 +23,9 @@ follow:
 * ``sirt``, ``ossart`` -- Kaczmarz-type methods (Sec. 2.1) with the ordered
   subsets update (Sec. 2.2.2, Eq. 6).
 * ``cgls`` -- CGLS (Sec. 2.1, Krylov methods; Hestenes and Stiefel).
+* ``tv`` -- AwTV (the adaptive-weighted TV of Sec. 2.2's algorithm features,
+  extended to volumes), its gradient, TV steepest descent and ASD-POCS /
+  OS-ASD-POCS (Sec. 2.1, POCS methods; Sidky and Pan).
 * ``mlem``, ``osem`` -- MLEM (Sec. 2.1, Eq. 5) and its ordered-subsets form
   (statistical methods; Hudson and Larkin), with either projector pair.
 * ``conv`` -- the 3x3x3 convolutions of the learned-gradient network and
