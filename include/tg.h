@@ -313,6 +313,47 @@ tg_status tg_osem(const tg_geometry *geo, const double *angles, int nAngles, con
                   float *vol, int niter, int blocksize, int order, uint64_t seed, int method,
                   double *resid_hist, void *stream);
 
+/* Parameters of ASD-POCS (Sidky and Pan 2008; Sec. 2.1, POCS methods). */
+typedef struct {
+    int niter;        /* outer iterations */
+    int blocksize;    /* angles per OS-SART block of the data step (1: SART, ASD-POCS) */
+    int tv_steps;     /* TV steepest-descent steps per iteration (ng) */
+    float alpha;      /* first TV step = alpha * ||data-step change|| */
+    float alpha_red;  /* TV step reduction */
+    float r_max;      /* reduce when ||TV change|| > r_max ||data-step change|| ... */
+    float data_tol;   /* ... and ||A x - b|| > data_tol */
+    float beta;       /* OS-SART relaxation of the first iteration */
+    float beta_red;   /* relaxation reduction per iteration */
+    float delta;      /* AwTV weight scale (INFINITY: plain TV) */
+    float eps;        /* TV smoothing constant under the square root (> 0) */
+} tg_pocs_params;
+
+/* ASD-POCS / OS-ASD-POCS: per iteration, x_prev = x; an OS-SART sweep
+ * (A = TG_INTERP, A^T = TG_MATCHED, blocks of `blocksize` in acquisition
+ * order) with relaxation beta and the clamp at 0; dd = ||A x - b||,
+ * dp = ||x - x_prev||; on the first iteration dtvg = alpha dp; tv_steps
+ * steps x <- x - dtvg g/||g|| with g the AwTV gradient (tg_tv_gradient);
+ * dg = the TV steps' change; dtvg *= alpha_red when dg > r_max dp and
+ * dd > data_tol; beta *= beta_red.  The step control runs on the device.
+ * vol: x0 in, x out.  resid_hist (nullable): dd after each iteration. */
+tg_status tg_asd_pocs(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                      float *vol, const tg_pocs_params *params, double *resid_hist, void *stream);
+
+/* Gradient of AwTV (Sec. 2.2 algorithm features, extended to volumes) with
+ * the weights held constant: backward differences d_a(v) = x(v) - x(v - e_a)
+ * (0 across the lower faces), w_a = exp(-(d_a/delta)^2) (delta = INFINITY:
+ * w = 1, plain TV), n(v) = sqrt(sum_a w_a d_a^2 + eps),
+ * g(v) = sum_a w_a(v) d_a(v)/n(v) - sum_a w_a(v+e_a) d_a(v+e_a)/n(v+e_a).
+ * vol, grad: distinct device buffers [nz][ny][nx]; dims = {nx, ny, nz},
+ * nz <= 65535. */
+tg_status tg_tv_gradient(const float *vol, float *grad, const int32_t *dims, float delta, float eps,
+                         void *stream);
+
+/* `steps` normalised steepest-descent steps on AwTV, in place:
+ * vol <- vol - step g/||g|| (unchanged where ||g|| = 0).  Device buffer. */
+tg_status tg_tv_descent(float *vol, const int32_t *dims, int steps, float step, float delta, float eps,
+                        void *stream);
+
 /* Bytes of device scratch a call would take (op: 0 forward, 1 backproject,
  * 2 fdk, 3 sirt, 4 ossart, 5 cgls, 6 mlem, 7 osem; blocksize only for
  * ossart and osem). */

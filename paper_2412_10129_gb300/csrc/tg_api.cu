@@ -154,6 +154,78 @@ uint64_t splitmix64(uint64_t &x) {
     return z ^ (z >> 31);
 }
 
+// The SART weights of a call and one sweep over its blocks (Sec. 2.2.2,
+// Eq. 6): W = 1/(A 1) per ray, V_s = 1/(A_s^T 1) per voxel and block.
+struct Sart {
+    std::vector<Block> blocks;
+    float *W = nullptr, *r = nullptr, *V = nullptr;
+    unsigned int *amax = nullptr;
+    size_t nvox = 0, nray = 0;
+
+    void init(Call &c, const Grid &g, const Angle *dA, int nA, int blocksize, size_t nv, size_t nr) {
+        nvox = nv;
+        nray = nr;
+        blocks = make_blocks(nA, blocksize);
+        W = c.alloc<float>(nray);
+        r = c.alloc<float>(nray);
+        float *ones = c.alloc<float>(nvox > nray ? nvox : nray);
+        V = c.alloc<float>(nvox * blocks.size());
+        amax = c.alloc<unsigned int>(1);
+        if (!c.ok()) return;
+        c.ok(launch_fill(ones, 1.f, nvox > nray ? nvox : nray, c.s));
+        c.ok(launch_forward(TG_INTERP, g, dA, ones, W, 1, FP_STORE, FpEpilogue{}, c.s));
+        c.ok(launch_safe_inverse(W, nray, c.s));
+        for (size_t k = 0; k < blocks.size() && c.ok(); ++k) {
+            Grid gs = g;
+            gs.nA = blocks[k].size;
+            // V and the updates below are divided voxel by voxel, so these
+            // backprojections keep FP32 accumulation (see tg_backproject.cu)
+            BpEpilogue e{};
+            e.scale = g.delta;
+            e.absmax = amax;
+            e.fp32_acc = 1;
+            c.ok(launch_backproject(TG_MATCHED, gs, dA + blocks[k].start, ones, V + k * nvox, 1, BP_STORE, e, c.s));
+            c.ok(launch_safe_inverse(V + k * nvox, nvox, c.s));
+        }
+    }
+
+    // x <- P(x + lambda V_s A_s^T W_s (b_s - A_s x)) for the blocks in order perm.
+    void sweep(Call &c, const Grid &g, const Angle *dA, const float *b, float *x, float lambda, int nonneg,
+               const std::vector<int> &perm) {
+        const size_t plane = (size_t)g.nu * g.nv;
+        for (size_t q = 0; q < perm.size() && c.ok(); ++q) {
+            const Block &B = blocks[perm[q]];
+            Grid gs = g;
+            gs.nA = B.size;
+            FpEpilogue fe{};
+            fe.b = b + (size_t)B.start * plane;
+            fe.W = W + (size_t)B.start * plane;
+            c.ok(launch_forward(TG_INTERP, gs, dA + B.start, x, r, 1, FP_RESID_W, fe, c.s));
+            BpEpilogue be{};
+            be.Vw = V + (size_t)perm[q] * nvox;
+            be.lambda = lambda;
+            be.nonneg = nonneg;
+            be.scale = g.delta;
+            be.absmax = amax;
+            be.fp32_acc = 1;
+            c.ok(launch_backproject(TG_MATCHED, gs, dA + B.start, r, x, 1, BP_SIRT, be, c.s));
+        }
+    }
+};
+
+// Block order of one iteration: acquisition order, or a Fisher-Yates
+// shuffle driven by SplitMix64.
+void block_order(std::vector<int> &perm, int order, uint64_t &rng) {
+    for (size_t k = 0; k < perm.size(); ++k) perm[k] = (int)k;
+    if (order == TG_ORDER_RANDOM)
+        for (size_t k = perm.size(); k > 1; --k) {
+            const size_t j = (size_t)(splitmix64(rng) % k);
+            int t = perm[k - 1];
+            perm[k - 1] = perm[j];
+            perm[j] = t;
+        }
+}
+
 // Shared body of SIRT and OS-SART (SIRT = one block holding every angle).
 tg_status sart_family(const tg_geometry *geo, const double *angles, int nA, const float *proj, float *vol,
                       int niter, int blocksize, int order, uint64_t seed, float lambda, int nonneg,
@@ -183,67 +255,92 @@ tg_status sart_family(const tg_geometry *geo, const double *angles, int nA, cons
     }
     Angle *dA = upload_angles(c, geo, angles, nA);
     const Grid g = call_grid(geo, angles, nA);
-    const auto blocks = make_blocks(nA, blocksize);
-    float *W = c.alloc<float>(nray);
-    float *r = c.alloc<float>(nray);
-    float *ones = c.alloc<float>(nvox > nray ? nvox : nray);
-    float *V = c.alloc<float>(nvox * blocks.size());
     double *acc = c.alloc<double>(4);
-    unsigned int *amax = c.alloc<unsigned int>(1);
+    Sart sart;
+    if (c.ok()) sart.init(c, g, dA, nA, blocksize, nvox, nray);
     if (!c.ok()) return c.finish();
-    // W = 1 / (A 1) per ray, V_s = 1 / (A_s^T 1) per voxel and block.
-    c.ok(launch_fill(ones, 1.f, nvox > nray ? nvox : nray, c.s));
-    c.ok(launch_forward(TG_INTERP, g, dA, ones, W, 1, FP_STORE, FpEpilogue{}, c.s));
-    c.ok(launch_safe_inverse(W, nray, c.s));
-    const size_t plane = (size_t)g.nu * g.nv;
-    for (size_t k = 0; k < blocks.size() && c.ok(); ++k) {
-        Grid gs = g;
-        gs.nA = blocks[k].size;
-        // V and the updates below are divided voxel by voxel, so these
-        // backprojections keep FP32 accumulation (see tg_backproject.cu)
-        BpEpilogue e{};
-        e.scale = g.delta;
-        e.absmax = amax;
-        e.fp32_acc = 1;
-        c.ok(launch_backproject(TG_MATCHED, gs, dA + blocks[k].start, ones, V + k * nvox, 1, BP_STORE, e, c.s));
-        c.ok(launch_safe_inverse(V + k * nvox, nvox, c.s));
-    }
     uint64_t rng = seed;
-    std::vector<int> perm(blocks.size());
+    std::vector<int> perm(sart.blocks.size());
     for (int it = 0; it < niter && c.ok(); ++it) {
-        for (size_t k = 0; k < perm.size(); ++k) perm[k] = (int)k;
-        if (order == TG_ORDER_RANDOM)
-            for (size_t k = perm.size(); k > 1; --k) {
-                const size_t j = (size_t)(splitmix64(rng) % k);
-                int t = perm[k - 1];
-                perm[k - 1] = perm[j];
-                perm[j] = t;
-            }
-        for (size_t q = 0; q < perm.size() && c.ok(); ++q) {
-            const Block &B = blocks[perm[q]];
-            Grid gs = g;
-            gs.nA = B.size;
-            FpEpilogue fe{};
-            fe.b = b.dev + (size_t)B.start * plane;
-            fe.W = W + (size_t)B.start * plane;
-            c.ok(launch_forward(TG_INTERP, gs, dA + B.start, x.dev, r, 1, FP_RESID_W, fe, c.s));
-            BpEpilogue be{};
-            be.Vw = V + (size_t)perm[q] * nvox;
-            be.lambda = lambda;
-            be.nonneg = nonneg;
-            be.scale = g.delta;
-            be.absmax = amax;
-            be.fp32_acc = 1;
-            c.ok(launch_backproject(TG_MATCHED, gs, dA + B.start, r, x.dev, 1, BP_SIRT, be, c.s));
-        }
+        block_order(perm, order, rng);
+        sart.sweep(c, g, dA, b.dev, x.dev, lambda, nonneg, perm);
         if (hist && c.ok()) {
             c.ok(cudaMemsetAsync(acc, 0, sizeof(double), c.s));
             FpEpilogue fe{};
             fe.b = b.dev;
             fe.norm = acc;
-            c.ok(launch_forward(TG_INTERP, g, dA, x.dev, r, 1, FP_RESID_NORM, fe, c.s));
+            c.ok(launch_forward(TG_INTERP, g, dA, x.dev, sart.r, 1, FP_RESID_NORM, fe, c.s));
             c.ok(launch_sqrt_copy(acc, hist + it, c.s));
         }
+    }
+    stage_out(c, x);
+    if (host_hist && c.ok())
+        c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+    return c.finish();
+}
+
+// ASD-POCS / OS-ASD-POCS (Sidky and Pan): an OS-SART sweep with relaxation
+// beta and the non-negativity clamp, then tv_steps normalised AwTV descent
+// steps whose length dtvg adapts on the device (k_pocs_control).
+tg_status asd_pocs(const tg_geometry *geo, const double *angles, int nA, const float *proj, float *vol,
+                   const tg_pocs_params *P, double *resid_hist, void *stream) {
+    tg_status st = check_common(geo, angles, nA);
+    if (st != TG_OK) return st;
+    if (!P || P->niter < 0 || P->blocksize <= 0 || P->tv_steps < 0 || !vol || (nA > 0 && !proj)) return TG_ERR_ARG;
+    if (!isfinite(P->alpha) || !isfinite(P->alpha_red) || !isfinite(P->r_max) || !isfinite(P->beta) ||
+        !isfinite(P->beta_red) || !(P->eps > 0.f) || !isfinite(P->eps) || isnan(P->delta) || !(P->delta > 0.f) ||
+        isnan(P->data_tol))
+        return TG_ERR_ARG;
+    if (!tv_dims_ok(geo->nVoxel[0], geo->nVoxel[1], geo->nVoxel[2])) return TG_ERR_UNSUPPORTED;
+    if (P->niter == 0) return TG_OK;
+    const int niter = P->niter;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nA);
+    Call c(stream);
+    View<const float> b = stage_in(c, proj, nray, true);
+    View<float> x = stage_in(c, vol, nvox, true);
+    const bool host_hist = resid_hist && is_host(resid_hist);
+    double *hist = resid_hist;
+    if (host_hist) {
+        hist = c.alloc<double>((size_t)niter);
+        c.sync_at_end = true;
+    }
+    if (nA == 0) {
+        if (hist && c.ok()) c.ok(cudaMemsetAsync(hist, 0, sizeof(double) * niter, c.s));
+        stage_out(c, x);
+        if (host_hist && c.ok())
+            c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+        return c.finish();
+    }
+    Angle *dA = upload_angles(c, geo, angles, nA);
+    const Grid g = call_grid(geo, angles, nA);
+    float *prev = c.alloc<float>(nvox);  // x before the data step, then after it
+    float *tmp = c.alloc<float>(nvox);
+    double *sc = c.alloc<double>(4);     // dd^2, dp^2, dg^2, ||g||^2
+    float *dtvg = c.alloc<float>(1);
+    Sart sart;
+    if (c.ok()) sart.init(c, g, dA, nA, P->blocksize, nvox, nray);
+    if (!c.ok()) return c.finish();
+    c.ok(cudaMemcpyAsync(prev, x.dev, nvox * sizeof(float), cudaMemcpyDeviceToDevice, c.s));
+    c.ok(cudaMemsetAsync(dtvg, 0, sizeof(float), c.s));
+    std::vector<int> perm(sart.blocks.size());
+    uint64_t rng = 0;
+    float beta = P->beta;
+    const int nx = geo->nVoxel[0], ny = geo->nVoxel[1], nz = geo->nVoxel[2];
+    for (int it = 0; it < niter && c.ok(); ++it) {
+        block_order(perm, TG_ORDER_SEQUENTIAL, rng);
+        sart.sweep(c, g, dA, b.dev, x.dev, beta, 1, perm);
+        c.ok(cudaMemsetAsync(sc, 0, 3 * sizeof(double), c.s));
+        FpEpilogue fe{};
+        fe.b = b.dev;
+        fe.norm = sc;  // dd^2
+        c.ok(launch_forward(TG_INTERP, g, dA, x.dev, sart.r, 1, FP_RESID_NORM, fe, c.s));
+        c.ok(launch_diff_norm_copy(x.dev, prev, nvox, sc + 1, c.s));  // dp^2; prev = x (after the data step)
+        c.ok(launch_pocs_control(sc, dtvg, 0, it == 0, P->alpha, P->alpha_red, P->r_max, P->data_tol, c.s));
+        c.ok(launch_tv_descent(x.dev, tmp, sc + 3, nx, ny, nz, P->tv_steps, 0.f, dtvg, P->delta, P->eps, c.s));
+        c.ok(launch_diff_norm_copy(x.dev, prev, nvox, sc + 2, c.s));  // dg^2; prev = x (before the next data step)
+        c.ok(launch_pocs_control(sc, dtvg, 1, 0, P->alpha, P->alpha_red, P->r_max, P->data_tol, c.s));
+        if (hist) c.ok(launch_sqrt_copy(sc, hist + it, c.s));
+        beta *= P->beta_red;
     }
     stage_out(c, x);
     if (host_hist && c.ok())
@@ -307,14 +404,7 @@ tg_status em_family(const tg_geometry *geo, const double *angles, int nA, const 
     uint64_t rng = seed;
     std::vector<int> perm(blocks.size());
     for (int it = 0; it < niter && c.ok(); ++it) {
-        for (size_t k = 0; k < perm.size(); ++k) perm[k] = (int)k;
-        if (order == TG_ORDER_RANDOM)
-            for (size_t k = perm.size(); k > 1; --k) {
-                const size_t j = (size_t)(splitmix64(rng) % k);
-                int t = perm[k - 1];
-                perm[k - 1] = perm[j];
-                perm[j] = t;
-            }
+        block_order(perm, order, rng);
         for (size_t q = 0; q < perm.size() && c.ok(); ++q) {
             const Block &B = blocks[perm[q]];
             Grid gs = g;
@@ -666,6 +756,38 @@ tg_status tg_osem(const tg_geometry *geo, const double *angles, int nAngles, con
                   int niter, int blocksize, int order, uint64_t seed, int method, double *resid_hist,
                   void *stream) {
     return em_family(geo, angles, nAngles, proj, vol, niter, blocksize, order, seed, method, resid_hist, stream);
+}
+
+tg_status tg_asd_pocs(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                      const tg_pocs_params *params, double *resid_hist, void *stream) {
+    return asd_pocs(geo, angles, nAngles, proj, vol, params, resid_hist, stream);
+}
+
+tg_status tg_tv_gradient(const float *vol, float *grad, const int32_t *dims, float delta, float eps,
+                         void *stream) {
+    if (!vol || !grad || !dims || (const void *)vol == (const void *)grad) return TG_ERR_ARG;
+    if (!(eps > 0.f) || !isfinite(eps) || isnan(delta) || !(delta > 0.f)) return TG_ERR_ARG;
+    if (!tv_dims_ok(dims[0], dims[1], dims[2])) return TG_ERR_ARG;
+    if (is_host(vol) || is_host(grad)) return TG_ERR_ARG;
+    Call c(stream);
+    c.ok(launch_tv_gradient(vol, grad, dims[0], dims[1], dims[2], delta, eps, c.s));
+    return c.finish();
+}
+
+tg_status tg_tv_descent(float *vol, const int32_t *dims, int steps, float step, float delta, float eps,
+                        void *stream) {
+    if (!vol || !dims || steps < 0 || !isfinite(step)) return TG_ERR_ARG;
+    if (!(eps > 0.f) || !isfinite(eps) || isnan(delta) || !(delta > 0.f)) return TG_ERR_ARG;
+    if (!tv_dims_ok(dims[0], dims[1], dims[2])) return TG_ERR_ARG;
+    if (is_host(vol)) return TG_ERR_ARG;
+    if (steps == 0) return TG_OK;
+    const size_t n = (size_t)dims[0] * dims[1] * dims[2];
+    Call c(stream);
+    float *tmp = c.alloc<float>(n);
+    double *norm = c.alloc<double>(1);
+    if (!c.ok()) return c.finish();
+    c.ok(launch_tv_descent(vol, tmp, norm, dims[0], dims[1], dims[2], steps, step, nullptr, delta, eps, c.s));
+    return c.finish();
 }
 
 tg_status tg_cgls(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,

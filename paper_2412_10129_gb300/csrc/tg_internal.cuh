@@ -194,5 +194,15 @@ cudaError_t launch_cgls_p(float *p, const float *sv, size_t nvox, double *scal, 
 cudaError_t launch_cgls_rotate(double *scal, double *hist_slot, cudaStream_t s);
 cudaError_t launch_cgls_init(double *scal, cudaStream_t s);
 cudaError_t launch_sqrt_copy(const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_diff_norm_copy(const float *a, float *b, size_t n, double *acc, cudaStream_t s);
+cudaError_t launch_pocs_control(const double *sc, float *dtvg, int phase, int first, float alpha, float alpha_red,
+                                float r_max, float data_tol, cudaStream_t s);
+
+// Total variation (tg_tv.cu).
+bool tv_dims_ok(int nx, int ny, int nz);
+cudaError_t launch_tv_gradient(const float *x, float *grad, int nx, int ny, int nz, float delta, float eps,
+                               cudaStream_t s);
+cudaError_t launch_tv_descent(float *x, float *tmp, double *norm, int nx, int ny, int nz, int steps, float step,
+                              const float *step_dev, float delta, float eps, cudaStream_t s);
 
 }  // namespace tg

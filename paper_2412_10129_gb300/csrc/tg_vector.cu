@@ -102,6 +102,34 @@ __global__ void k_sqrt_copy(const double *src, double *dst) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = sqrt(*src);
 }
 
+// acc += ||a - b||^2, then b = a (ASD-POCS: the distance a step moved x,
+// and the copy the next distance is measured from).
+__global__ void k_diff_norm_copy(const float *a, float *b, size_t n, double *acc) {
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const float v = a[i];
+        const double d = (double)v - (double)b[i];
+        s += d * d;
+        b[i] = v;
+    }
+    block_sum(s, acc);
+}
+
+// ASD-POCS step control (Sidky and Pan) on device scalars
+// sc = {dd^2, dp^2, dg^2}: phase 0 after the data step sets the TV step
+// dtvg = alpha dp on the first iteration; phase 1 after the TV steps
+// shrinks it by alpha_red when dg > r_max dp and dd > data_tol.
+__global__ void k_pocs_control(const double *sc, float *dtvg, int phase, int first, float alpha, float alpha_red,
+                               float r_max, float data_tol) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double dd = sqrt(sc[0]), dp = sqrt(sc[1]), dg = sqrt(sc[2]);
+    if (phase == 0) {
+        if (first) *dtvg = (float)(alpha * dp);
+    } else if (dg > (double)r_max * dp && dd > (double)data_tol) {
+        *dtvg = *dtvg * alpha_red;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_safe_inverse(float *a, size_t n, cudaStream_t s) {
@@ -159,6 +187,20 @@ cudaError_t launch_cgls_init(double *scal, cudaStream_t s) {
 
 cudaError_t launch_sqrt_copy(const double *src, double *dst, cudaStream_t s) {
     k_sqrt_copy<<<1, 32, 0, s>>>(src, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diff_norm_copy(const float *a, float *b, size_t n, double *acc, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_diff_norm_copy<<<blocks_for(n), TPB, 0, s>>>(a, b, n, acc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pocs_control(const double *sc, float *dtvg, int phase, int first, float alpha, float alpha_red,
+                                float r_max, float data_tol, cudaStream_t s) {
+    k_pocs_control<<<1, 32, 0, s>>>(sc, dtvg, phase, first, alpha, alpha_red, r_max, data_tol);
     count_launch();
     return cudaGetLastError();
 }

@@ -28,6 +28,13 @@ _STATUS = {0: "ok", 1: "invalid argument", 2: "invalid geometry", 3: "device out
            4: "CUDA error", 5: "device wait timed out", 6: "unsupported request"}
 
 
+class _PocsParams(ctypes.Structure):
+    _fields_ = [("niter", ctypes.c_int), ("blocksize", ctypes.c_int), ("tv_steps", ctypes.c_int),
+                ("alpha", ctypes.c_float), ("alpha_red", ctypes.c_float), ("r_max", ctypes.c_float),
+                ("data_tol", ctypes.c_float), ("beta", ctypes.c_float), ("beta_red", ctypes.c_float),
+                ("delta", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
 class TgError(RuntimeError):
     def __init__(self, fn, code):
         super().__init__(f"{fn} failed: {_STATUS.get(code, code)} (status {code})")
@@ -76,6 +83,10 @@ def load():
                           ctypes.c_uint64, ctypes.c_float, ctypes.c_int, _DP, _VP],
             "tg_cgls": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
             "tg_mlem": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _DP, _VP],
+            "tg_asd_pocs": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_PocsParams), _DP, _VP],
+            "tg_tv_gradient": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_float, ctypes.c_float, _VP],
+            "tg_tv_descent": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, _VP],
             "tg_osem": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                         ctypes.c_int, _DP, _VP],
             "tg_workspace_size": [G, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -417,6 +428,46 @@ def osem(geo, proj, niter: int, blocksize: int = 20, order: str = "sequential", 
         _sync(proj)
         return x, h[:niter]
     return x
+
+
+def asd_pocs(geo, proj, niter: int, blocksize: int = 1, tv_steps: int = 20, alpha: float = 0.002,
+             alpha_red: float = 0.95, r_max: float = 0.95, data_tol: float = 0.0, beta: float = 1.0,
+             beta_red: float = 0.995, delta: float = float("inf"), eps: float = 1e-8, x0=None,
+             resid: bool = False, stream=None):
+    """ASD-POCS (blocksize 1) / OS-ASD-POCS with plain TV or AwTV (finite
+    ``delta``); returns x (and ||A x_k - b|| after each data step)."""
+    G = _Geo(geo)
+    x = _x0(geo, proj, x0)
+    h, hp = _hist(niter, resid)
+    P = _PocsParams(int(niter), int(blocksize), int(tv_steps), alpha, alpha_red, r_max, data_tol, beta, beta_red,
+                    delta, eps)
+    _check("tg_asd_pocs", load().tg_asd_pocs(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), ctypes.byref(P), hp,
+                                             _stream(proj, stream)))
+    if resid:
+        _sync(proj)
+        return x, h[:niter]
+    return x
+
+
+def _dims(vol):
+    nz, ny, nx = vol.shape[-3:]
+    return (ctypes.c_int32 * 3)(int(nx), int(ny), int(nz))
+
+
+def tv_gradient(vol, delta: float = float("inf"), eps: float = 1e-8, out=None, stream=None):
+    """Gradient of (Aw)TV with frozen weights; CUDA tensors [nz, ny, nx]."""
+    if out is None:
+        out = _torch().empty_like(vol)
+    _check("tg_tv_gradient", load().tg_tv_gradient(_ptr(vol), _ptr(out), _dims(vol), delta, eps,
+                                                   _stream(vol, stream)))
+    return out
+
+
+def tv_descent(vol, steps: int, step: float, delta: float = float("inf"), eps: float = 1e-8, stream=None):
+    """``steps`` normalised (Aw)TV descent steps on a CUDA tensor, in place."""
+    _check("tg_tv_descent", load().tg_tv_descent(_ptr(vol), _dims(vol), int(steps), step, delta, eps,
+                                                 _stream(vol, stream)))
+    return vol
 
 
 def workspace_size(geo, op: str, batch: int = 1, blocksize: int = 20) -> int:
