@@ -26,6 +26,7 @@ follow:
 * ``tv`` -- AwTV (the adaptive-weighted TV of Sec. 2.2's algorithm features,
   extended to volumes), its gradient, TV steepest descent and ASD-POCS /
   OS-ASD-POCS (Sec. 2.1, POCS methods; Sidky and Pan).
+* ``lsqr`` -- LSQR (Sec. 2.1, Krylov methods; Paige and Saunders 1982).
 * ``mlem``, ``osem`` -- MLEM (Sec. 2.1, Eq. 5) and its ordered-subsets form
   (statistical methods; Hudson and Larkin), with either projector pair.
 * ``conv`` -- the 3x3x3 convolutions of the learned-gradient network and
@@ -36,6 +37,7 @@ follow:
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -387,3 +389,54 @@ def poisson_loglik(geo, x, b, method: str = "interp") -> float:
     b = _f64(b).reshape(y.shape)
     m = y > 0
     return float(np.sum(b[m] * np.log(y[m]) - y[m]))
+
+
+# ---------------------------------------------------------------------------
+# LSQR (Sec. 2.1, Krylov methods; Paige and Saunders 1982).
+# ---------------------------------------------------------------------------
+
+def lsqr(geo, b, niter: int, x0=None):
+    """LSQR on min ||A x - b|| (A interpolated, A^T matched), the steps of
+    Paige and Saunders' algorithm:
+        beta u = r0 = b - A x0,  alpha v = A^T u,  w = v,
+        phibar = beta,  rhobar = alpha
+        repeat: beta u = A v - alpha u;   alpha v = A^T u - beta v
+                rho = sqrt(rhobar^2 + beta^2); c = rhobar/rho; s = beta/rho
+                theta = s alpha; rhobar = -c alpha; phi = c phibar; phibar = s phibar
+                x += (phi/rho) w;  w = v - (theta/rho) w
+    A zero beta or alpha ends the recurrence (x is then exact).  Returns (x,
+    phibar after each iteration, which equals ||b - A x_k||)."""
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    b = _f64(b)
+    x = np.zeros((nz, ny, nx)) if x0 is None else _f64(x0).copy()
+    u = b - forward(geo, x)
+    beta = float(np.linalg.norm(u))
+    u = u / beta if beta > 0 else u
+    v = backproject(geo, u, "matched")
+    alpha = float(np.linalg.norm(v))
+    v = v / alpha if alpha > 0 else v
+    w = v.copy()
+    phibar, rhobar = beta, alpha
+    hist = []
+    for _ in range(niter):
+        if beta == 0.0 or alpha == 0.0:
+            hist.append(phibar)
+            continue
+        u = forward(geo, v) - alpha * u
+        beta = float(np.linalg.norm(u))
+        if beta > 0:
+            u = u / beta
+        v = backproject(geo, u, "matched") - beta * v
+        alpha = float(np.linalg.norm(v))
+        if alpha > 0:
+            v = v / alpha
+        rho = math.hypot(rhobar, beta)
+        c, s = rhobar / rho, beta / rho
+        theta = s * alpha
+        rhobar = -c * alpha
+        phi = c * phibar
+        phibar = s * phibar
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+        hist.append(phibar)
+    return x, np.array(hist)
