@@ -313,6 +313,17 @@ tg_status tg_osem(const tg_geometry *geo, const double *angles, int nAngles, con
                   float *vol, int niter, int blocksize, int order, uint64_t seed, int method,
                   double *resid_hist, void *stream);
 
+/* LSQR (Sec. 2.1, Krylov methods; Paige and Saunders 1982) on
+ * min ||A x - b||, A = TG_INTERP, A^T = TG_MATCHED: Golub-Kahan
+ * bidiagonalisation beta u = A v - alpha u, alpha v = A^T u - beta v with
+ * the plane rotations and the x, w updates of the paper; FP64 norms and
+ * scalars on the device.  vol: x0 in, x out.  resid_hist (nullable):
+ * phibar after each iteration, the recurrence's value of ||b - A x_k||
+ * (free: no extra projection).  Same iterates as tg_cgls in exact
+ * arithmetic. */
+tg_status tg_lsqr(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                  float *vol, int niter, double *resid_hist, void *stream);
+
 /* Parameters of ASD-POCS (Sidky and Pan 2008; Sec. 2.1, POCS methods). */
 typedef struct {
     int niter;        /* outer iterations */

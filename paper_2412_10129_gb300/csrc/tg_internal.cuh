@@ -194,6 +194,13 @@ cudaError_t launch_cgls_p(float *p, const float *sv, size_t nvox, double *scal, 
 cudaError_t launch_cgls_rotate(double *scal, double *hist_slot, cudaStream_t s);
 cudaError_t launch_cgls_init(double *scal, cudaStream_t s);
 cudaError_t launch_sqrt_copy(const double *src, double *dst, cudaStream_t s);
+// LSQR scalars and vector updates (tg_vector.cu; slots listed there).
+cudaError_t launch_lsqr_axpy(float *y, const float *p, size_t n, double *L, int k, cudaStream_t s);
+cudaError_t launch_lsqr_finish(double *L, int k, cudaStream_t s);
+cudaError_t launch_lsqr_scale(float *y, size_t n, const double *L, int k, cudaStream_t s);
+cudaError_t launch_lsqr_start(double *L, cudaStream_t s);
+cudaError_t launch_lsqr_givens(double *L, double *hist, cudaStream_t s);
+cudaError_t launch_lsqr_vxw(float *v, float *x, float *w, size_t n, const double *L, cudaStream_t s);
 cudaError_t launch_diff_norm_copy(const float *a, float *b, size_t n, double *acc, cudaStream_t s);
 cudaError_t launch_pocs_control(const double *sc, float *dtvg, int phase, int first, float alpha, float alpha_red,
                                 float r_max, float data_tol, cudaStream_t s);

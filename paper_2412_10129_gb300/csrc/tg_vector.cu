@@ -102,6 +102,79 @@ __global__ void k_sqrt_copy(const double *src, double *dst) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = sqrt(*src);
 }
 
+// LSQR (Paige and Saunders) scalar slots: L[0] alpha, L[1] beta, L[2]
+// rhobar, L[3] phibar, L[4] norm accumulator, L[5] phi/rho (x step),
+// L[6] theta/rho (w step).
+
+// y = p - L[k] y ; L[4] += ||y||^2
+__global__ void k_lsqr_axpy(float *y, const float *p, size_t n, double *L, int k) {
+    const float a = (float)L[k];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const float v = fmaf(-a, y[i], p[i]);
+        y[i] = v;
+        s += (double)v * (double)v;
+    }
+    block_sum(s, L + 4);
+}
+
+// L[k] = sqrt(L[4]); L[4] = 0
+__global__ void k_lsqr_finish(double *L, int k) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        L[k] = sqrt(L[4]);
+        L[4] = 0.0;
+    }
+}
+
+// y /= L[k] where L[k] > 0
+__global__ void k_lsqr_scale(float *y, size_t n, const double *L, int k) {
+    const double d = L[k];
+    if (!(d > 0.0)) return;
+    const float inv = (float)(1.0 / d);
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) y[i] *= inv;
+}
+
+// Start: rhobar = alpha, phibar = beta.
+__global__ void k_lsqr_start(double *L) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        L[2] = L[0];
+        L[3] = L[1];
+    }
+}
+
+// The plane rotation of one iteration (alpha, beta already updated);
+// hist (nullable) receives phibar = ||b - A x||.
+__global__ void k_lsqr_givens(double *L, double *hist) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double alpha = L[0], beta = L[1], rhobar = L[2], phibar = L[3];
+    const double rho = hypot(rhobar, beta);
+    if (rho > 0.0) {
+        const double c = rhobar / rho, s = beta / rho;
+        const double theta = s * alpha;
+        L[2] = -c * alpha;
+        L[3] = s * phibar;
+        L[5] = c * phibar / rho;
+        L[6] = theta / rho;
+    } else {  // the recurrence has ended: x is exact
+        L[5] = 0.0;
+        L[6] = 0.0;
+    }
+    if (hist) *hist = L[3];
+}
+
+// v /= alpha ; x += (phi/rho) w ; w = v - (theta/rho) w
+__global__ void k_lsqr_vxw(float *v, float *x, float *w, size_t n, const double *L) {
+    const double a = L[0];
+    const float inv = a > 0.0 ? (float)(1.0 / a) : 1.f;
+    const float cx = (float)L[5], cw = (float)L[6];
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const float vi = v[i] * inv, wi = w[i];
+        v[i] = vi;
+        x[i] = fmaf(cx, wi, x[i]);
+        w[i] = fmaf(-cw, wi, vi);
+    }
+}
+
 // acc += ||a - b||^2, then b = a (ASD-POCS: the distance a step moved x,
 // and the copy the next distance is measured from).
 __global__ void k_diff_norm_copy(const float *a, float *b, size_t n, double *acc) {
@@ -201,6 +274,43 @@ cudaError_t launch_diff_norm_copy(const float *a, float *b, size_t n, double *ac
 cudaError_t launch_pocs_control(const double *sc, float *dtvg, int phase, int first, float alpha, float alpha_red,
                                 float r_max, float data_tol, cudaStream_t s) {
     k_pocs_control<<<1, 32, 0, s>>>(sc, dtvg, phase, first, alpha, alpha_red, r_max, data_tol);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_axpy(float *y, const float *p, size_t n, double *L, int k, cudaStream_t s) {
+    k_lsqr_axpy<<<blocks_for(n), TPB, 0, s>>>(y, p, n, L, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_finish(double *L, int k, cudaStream_t s) {
+    k_lsqr_finish<<<1, 32, 0, s>>>(L, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_scale(float *y, size_t n, const double *L, int k, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_lsqr_scale<<<blocks_for(n), TPB, 0, s>>>(y, n, L, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_start(double *L, cudaStream_t s) {
+    k_lsqr_start<<<1, 32, 0, s>>>(L);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_givens(double *L, double *hist, cudaStream_t s) {
+    k_lsqr_givens<<<1, 32, 0, s>>>(L, hist);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_vxw(float *v, float *x, float *w, size_t n, const double *L, cudaStream_t s) {
+    k_lsqr_vxw<<<blocks_for(n), TPB, 0, s>>>(v, x, w, n, L);
     count_launch();
     return cudaGetLastError();
 }

@@ -83,6 +83,7 @@ def load():
                           ctypes.c_uint64, ctypes.c_float, ctypes.c_int, _DP, _VP],
             "tg_cgls": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
             "tg_mlem": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _DP, _VP],
+            "tg_lsqr": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
             "tg_asd_pocs": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_PocsParams), _DP, _VP],
             "tg_tv_gradient": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_float, ctypes.c_float, _VP],
             "tg_tv_descent": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_float, ctypes.c_float,
@@ -389,6 +390,18 @@ def cgls(geo, proj, niter: int, x0=None, resid: bool = False, stream=None):
     x = _x0(geo, proj, x0)
     h, hp = _hist(niter, resid)
     _check("tg_cgls", load().tg_cgls(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), int(niter), hp, _stream(proj, stream)))
+    if resid:
+        _sync(proj)
+        return x, h[:niter]
+    return x
+
+
+def lsqr(geo, proj, niter: int, x0=None, resid: bool = False, stream=None):
+    """LSQR; returns x (and the recurrence's ||b - A x_k|| when ``resid``)."""
+    G = _Geo(geo)
+    x = _x0(geo, proj, x0)
+    h, hp = _hist(niter, resid)
+    _check("tg_lsqr", load().tg_lsqr(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), int(niter), hp, _stream(proj, stream)))
     if resid:
         _sync(proj)
         return x, h[:niter]

@@ -128,3 +128,26 @@ def test_sirt_step_with_wide_dynamic_range(problem):
     assert rel_l2(x, xr) <= RTOL
     small = np.abs(xr) < np.percentile(np.abs(xr), 20)        # voxels dominated by small rays
     assert rel_l2(x[small], xr[small]) <= 1e-3
+
+
+def test_lsqr_20_iterations(problem):
+    """LSQR against the oracle's LSQR (iterates and the phibar residual
+    history), and against the GPU's own CGLS (the same Krylov iterates)."""
+    g, _, b = problem
+    x, hist = tg.lsqr(g, dev(b), 20, resid=True)
+    xr, hr = oracle.lsqr(g, b, 20)
+    assert rel_l2(host(x), xr) <= RTOL, rel_l2(host(x), xr)
+    np.testing.assert_allclose(hist, hr, rtol=RTOL)
+    xc = tg.cgls(g, dev(b), 20)
+    assert rel_l2(host(x), host(xc)) <= RTOL
+
+
+def test_lsqr_warm_start_and_zero_data(problem):
+    g, _, b = problem
+    x0 = dev(0.02 * np.random.default_rng(4).random(g.vol_shape))
+    x5 = tg.lsqr(g, dev(b), 5, x0=x0.clone())
+    xr, _ = oracle.lsqr(g, b, 5, x0=host(x0))
+    assert rel_l2(host(x5), xr) <= RTOL
+    # b = A x0 exactly reached: the recurrence ends and x stays x0
+    z = tg.lsqr(g, dev(np.zeros(g.proj_shape)), 3, x0=torch.zeros(g.vol_shape, device="cuda"))
+    assert torch.count_nonzero(z) == 0
