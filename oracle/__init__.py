@@ -27,6 +27,7 @@ follow:
   extended to volumes), its gradient, TV steepest descent and ASD-POCS /
   OS-ASD-POCS (Sec. 2.1, POCS methods; Sidky and Pan).
 * ``lsqr`` -- LSQR (Sec. 2.1, Krylov methods; Paige and Saunders 1982).
+* ``lsmr`` -- LSMR (Sec. 2.1, Krylov methods; Fong and Saunders 2011).
 * ``mlem``, ``osem`` -- MLEM (Sec. 2.1, Eq. 5) and its ordered-subsets form
   (statistical methods; Hudson and Larkin), with either projector pair.
 * ``conv`` -- the 3x3x3 convolutions of the learned-gradient network and
@@ -439,4 +440,68 @@ def lsqr(geo, b, niter: int, x0=None):
         x = x + (phi / rho) * w
         w = v - (theta / rho) * w
         hist.append(phibar)
+    return x, np.array(hist)
+
+
+def lsmr(geo, b, niter: int, x0=None):
+    """LSMR on min ||A x - b|| without damping, the steps of Fong and
+    Saunders' algorithm (the same bidiagonalisation as LSQR, then two plane
+    rotations per iteration so that ||A^T r_k|| is minimised over the
+    Krylov space):
+        beta u = b - A x0, alpha v = A^T u; alphabar = alpha, zetabar = alpha beta,
+        rho = 1, rhobar = 1, cbar = 1, sbar = 0, h = v, hbar = 0
+        repeat: beta u = A v - alpha u;  alpha' v = A^T u - beta v
+                rho_old = rho; rho = sqrt(alphabar^2 + beta^2)
+                c = alphabar/rho; s = beta/rho; theta = s alpha'; alphabar = c alpha'
+                rhobar_old = rhobar; thetabar = sbar rho
+                rhobar = sqrt((cbar rho)^2 + theta^2)
+                cbar = cbar rho / rhobar; sbar = theta / rhobar
+                zeta = cbar zetabar; zetabar = -sbar zetabar
+                hbar = h - (thetabar rho / (rho_old rhobar_old)) hbar
+                x += (zeta / (rho rhobar)) hbar
+                h = v - (theta / rho) h;  alpha = alpha'
+    Returns (x, ||b - A x_k|| after each iteration, computed with one
+    extra projection)."""
+    nx, ny, nz = (int(v) for v in geo.nVoxel)
+    b = _f64(b)
+    x = np.zeros((nz, ny, nx)) if x0 is None else _f64(x0).copy()
+    u = b - forward(geo, x)
+    beta = float(np.linalg.norm(u))
+    u = u / beta if beta > 0 else u
+    v = backproject(geo, u, "matched")
+    alpha = float(np.linalg.norm(v))
+    v = v / alpha if alpha > 0 else v
+    alphabar, zetabar = alpha, alpha * beta
+    rho, rhobar, cbar, sbar = 1.0, 1.0, 1.0, 0.0
+    h = v.copy()
+    hbar = np.zeros_like(x)
+    hist = []
+    for _ in range(niter):
+        if alpha * beta == 0.0:
+            hist.append(float(np.linalg.norm(b - forward(geo, x))))
+            continue
+        u = forward(geo, v) - alpha * u
+        beta = float(np.linalg.norm(u))
+        if beta > 0:
+            u = u / beta
+        v = backproject(geo, u, "matched") - beta * v
+        alpha_new = float(np.linalg.norm(v))
+        if alpha_new > 0:
+            v = v / alpha_new
+        rho_old = rho
+        rho = math.hypot(alphabar, beta)
+        c, s = alphabar / rho, beta / rho
+        theta = s * alpha_new
+        alphabar = c * alpha_new
+        rhobar_old = rhobar
+        thetabar = sbar * rho
+        rhobar = math.hypot(cbar * rho, theta)
+        cbar, sbar = cbar * rho / rhobar, theta / rhobar
+        zeta = cbar * zetabar
+        zetabar = -sbar * zetabar
+        hbar = h - (thetabar * rho / (rho_old * rhobar_old)) * hbar
+        x = x + (zeta / (rho * rhobar)) * hbar
+        h = v - (theta / rho) * h
+        alpha = alpha_new
+        hist.append(float(np.linalg.norm(b - forward(geo, x))))
     return x, np.array(hist)
