@@ -324,6 +324,14 @@ tg_status tg_osem(const tg_geometry *geo, const double *angles, int nAngles, con
 tg_status tg_lsqr(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
                   float *vol, int niter, double *resid_hist, void *stream);
 
+/* LSMR (Sec. 2.1, Krylov methods; Fong and Saunders 2011), undamped: the
+ * bidiagonalisation of tg_lsqr followed by two plane rotations per
+ * iteration, so that x_k minimises ||A^T (b - A x)|| over the Krylov space;
+ * scalars in FP64 on the device.  vol: x0 in, x out.  resid_hist
+ * (nullable): ||A x_k - b|| after each iteration (one extra projection). */
+tg_status tg_lsmr(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
+                  float *vol, int niter, double *resid_hist, void *stream);
+
 /* Parameters of ASD-POCS (Sidky and Pan 2008; Sec. 2.1, POCS methods). */
 typedef struct {
     int niter;        /* outer iterations */

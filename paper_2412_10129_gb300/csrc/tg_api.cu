@@ -914,6 +914,83 @@ tg_status tg_lsqr(const tg_geometry *geo, const double *angles, int nAngles, con
     return c.finish();
 }
 
+tg_status tg_lsmr(const tg_geometry *geo, const double *angles, int nAngles, const float *proj, float *vol,
+                  int niter, double *resid_hist, void *stream) {
+    tg_status st = check_common(geo, angles, nAngles);
+    if (st != TG_OK) return st;
+    if (niter < 0 || !vol || (nAngles > 0 && !proj)) return TG_ERR_ARG;
+    if (niter == 0) return TG_OK;
+    const size_t nvox = vol_count(geo), nray = proj_count(geo, nAngles);
+    Call c(stream);
+    View<const float> b = stage_in(c, proj, nray, true);
+    View<float> x = stage_in(c, vol, nvox, true);
+    const bool host_hist = resid_hist && is_host(resid_hist);
+    double *hist = resid_hist;
+    if (host_hist) {
+        hist = c.alloc<double>((size_t)niter);
+        c.sync_at_end = true;
+    }
+    if (nAngles == 0) {
+        if (hist && c.ok()) c.ok(cudaMemsetAsync(hist, 0, sizeof(double) * niter, c.s));
+        stage_out(c, x);
+        if (host_hist && c.ok())
+            c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+        return c.finish();
+    }
+    Angle *dA = upload_angles(c, geo, angles, nAngles);
+    float *u = c.alloc<float>(nray);
+    float *q = c.alloc<float>(nray);
+    float *v = c.alloc<float>(nvox);
+    float *h = c.alloc<float>(nvox);
+    float *hbar = c.alloc<float>(nvox);
+    float *sv = c.alloc<float>(nvox);
+    double *L = c.alloc<double>(16);
+    unsigned int *amax = c.alloc<unsigned int>(1);
+    if (!c.ok()) return c.finish();
+    const Grid g = call_grid(geo, angles, nAngles);
+    BpEpilogue be{};
+    be.scale = g.delta;
+    be.absmax = amax;
+    // beta u = b - A x0 ; alpha v = A^T u ; h = v ; hbar = 0
+    c.ok(cudaMemsetAsync(L, 0, 16 * sizeof(double), c.s));
+    c.ok(launch_forward(TG_INTERP, g, dA, x.dev, u, 1, FP_STORE, FpEpilogue{}, c.s));
+    c.ok(launch_sub(b.dev, u, u, nray, c.s));
+    c.ok(launch_norm2(u, nray, L + 4, c.s));
+    c.ok(launch_lsqr_finish(L, 1, c.s));
+    c.ok(launch_lsqr_scale(u, nray, L, 1, c.s));
+    c.ok(launch_backproject(TG_MATCHED, g, dA, u, v, 1, BP_STORE, be, c.s));
+    c.ok(launch_norm2(v, nvox, L + 4, c.s));
+    c.ok(launch_lsqr_finish(L, 0, c.s));
+    c.ok(launch_lsqr_scale(v, nvox, L, 0, c.s));
+    c.ok(cudaMemcpyAsync(h, v, nvox * sizeof(float), cudaMemcpyDeviceToDevice, c.s));
+    c.ok(cudaMemsetAsync(hbar, 0, nvox * sizeof(float), c.s));
+    c.ok(launch_lsmr_start(L, c.s));
+    double *racc = L + 15;
+    for (int it = 0; it < niter && c.ok(); ++it) {
+        c.ok(launch_forward(TG_INTERP, g, dA, v, q, 1, FP_STORE, FpEpilogue{}, c.s));   // q = A v
+        c.ok(launch_lsqr_axpy(u, q, nray, L, 0, c.s));                                 // u = q - alpha u
+        c.ok(launch_lsqr_finish(L, 1, c.s));                                           // beta
+        c.ok(launch_lsqr_scale(u, nray, L, 1, c.s));
+        c.ok(launch_backproject(TG_MATCHED, g, dA, u, sv, 1, BP_STORE, be, c.s));      // sv = A^T u
+        c.ok(launch_lsqr_axpy(v, sv, nvox, L, 1, c.s));                                // v = sv - beta v
+        c.ok(launch_lsqr_finish(L, 12, c.s));                                          // new alpha
+        c.ok(launch_lsmr_rot(L, c.s));
+        c.ok(launch_lsmr_update(v, x.dev, h, hbar, nvox, L, c.s));
+        if (hist && c.ok()) {
+            c.ok(cudaMemsetAsync(racc, 0, sizeof(double), c.s));
+            FpEpilogue fe{};
+            fe.b = b.dev;
+            fe.norm = racc;
+            c.ok(launch_forward(TG_INTERP, g, dA, x.dev, q, 1, FP_RESID_NORM, fe, c.s));
+            c.ok(launch_sqrt_copy(racc, hist + it, c.s));
+        }
+    }
+    stage_out(c, x);
+    if (host_hist && c.ok())
+        c.ok(cudaMemcpyAsync(resid_hist, hist, sizeof(double) * niter, cudaMemcpyDeviceToHost, c.s));
+    return c.finish();
+}
+
 tg_status tg_count_samples(const tg_geometry *geo, const double *angles, int nAngles, int method, uint64_t *count,
                            void *stream) {
     tg_status st = check_common(geo, angles, nAngles);

@@ -201,6 +201,10 @@ cudaError_t launch_lsqr_scale(float *y, size_t n, const double *L, int k, cudaSt
 cudaError_t launch_lsqr_start(double *L, cudaStream_t s);
 cudaError_t launch_lsqr_givens(double *L, double *hist, cudaStream_t s);
 cudaError_t launch_lsqr_vxw(float *v, float *x, float *w, size_t n, const double *L, cudaStream_t s);
+cudaError_t launch_lsmr_start(double *L, cudaStream_t s);
+cudaError_t launch_lsmr_rot(double *L, cudaStream_t s);
+cudaError_t launch_lsmr_update(float *v, float *x, float *h, float *hbar, size_t n, const double *L,
+                               cudaStream_t s);
 cudaError_t launch_diff_norm_copy(const float *a, float *b, size_t n, double *acc, cudaStream_t s);
 cudaError_t launch_pocs_control(const double *sc, float *dtvg, int phase, int first, float alpha, float alpha_red,
                                 float r_max, float data_tol, cudaStream_t s);

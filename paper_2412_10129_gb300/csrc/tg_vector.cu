@@ -175,6 +175,78 @@ __global__ void k_lsqr_vxw(float *v, float *x, float *w, size_t n, const double 
     }
 }
 
+// LSMR (Fong and Saunders) slots, beside the bidiagonalisation's L[0]
+// alpha, L[1] beta, L[4] accumulator: L[2] alphabar, L[3] zetabar, L[5]
+// rho, L[6] rhobar, L[7] cbar, L[8] sbar, L[9..11] the hbar, x and h step
+// coefficients, L[12] the new alpha, L[13] ended, L[14] skip this update.
+__global__ void k_lsmr_start(double *L) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    L[2] = L[0];
+    L[3] = L[0] * L[1];
+    L[5] = 1.0;
+    L[6] = 1.0;
+    L[7] = 1.0;
+    L[8] = 0.0;
+    L[13] = L[0] * L[1] == 0.0 ? 1.0 : 0.0;
+    L[14] = 0.0;
+}
+
+// The two plane rotations of one iteration (beta and the new alpha set).
+__global__ void k_lsmr_rot(double *L) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (L[13] != 0.0) {  // ended in an earlier iteration: x stays
+        L[14] = 1.0;
+        return;
+    }
+    const double beta = L[1], an = L[12], alphabar = L[2];
+    const double rho_old = L[5], rhobar_old = L[6], cbar = L[7], sbar = L[8], zetabar = L[3];
+    const double rho = hypot(alphabar, beta);
+    if (!(rho > 0.0)) {
+        L[13] = 1.0;
+        L[14] = 1.0;
+        return;
+    }
+    const double c = alphabar / rho, s = beta / rho;
+    const double theta = s * an;
+    const double thetabar = sbar * rho;
+    const double rhobar = hypot(cbar * rho, theta);
+    if (!(rhobar > 0.0)) {
+        L[13] = 1.0;
+        L[14] = 1.0;
+        return;
+    }
+    const double cb = cbar * rho / rhobar, sb = theta / rhobar;
+    const double zeta = cb * zetabar;
+    L[9] = thetabar * rho / (rho_old * rhobar_old);
+    L[10] = zeta / (rho * rhobar);
+    L[11] = theta / rho;
+    L[2] = c * an;
+    L[3] = -sb * zetabar;
+    L[5] = rho;
+    L[6] = rhobar;
+    L[7] = cb;
+    L[8] = sb;
+    L[0] = an;
+    L[14] = 0.0;
+    if (an * beta == 0.0) L[13] = 1.0;  // the next iterations change nothing
+}
+
+// v /= alpha ; hbar = h - c9 hbar ; x += c10 hbar ; h = v - c11 h
+__global__ void k_lsmr_update(float *v, float *x, float *h, float *hbar, size_t n, const double *L) {
+    if (L[14] != 0.0) return;
+    const double a = L[0];
+    const float inv = a > 0.0 ? (float)(1.0 / a) : 1.f;
+    const float c9 = (float)L[9], c10 = (float)L[10], c11 = (float)L[11];
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const float vi = v[i] * inv, hi = h[i];
+        const float hb = fmaf(-c9, hbar[i], hi);
+        hbar[i] = hb;
+        x[i] = fmaf(c10, hb, x[i]);
+        h[i] = fmaf(-c11, hi, vi);
+        v[i] = vi;
+    }
+}
+
 // acc += ||a - b||^2, then b = a (ASD-POCS: the distance a step moved x,
 // and the copy the next distance is measured from).
 __global__ void k_diff_norm_copy(const float *a, float *b, size_t n, double *acc) {
@@ -311,6 +383,25 @@ cudaError_t launch_lsqr_givens(double *L, double *hist, cudaStream_t s) {
 
 cudaError_t launch_lsqr_vxw(float *v, float *x, float *w, size_t n, const double *L, cudaStream_t s) {
     k_lsqr_vxw<<<blocks_for(n), TPB, 0, s>>>(v, x, w, n, L);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsmr_start(double *L, cudaStream_t s) {
+    k_lsmr_start<<<1, 32, 0, s>>>(L);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsmr_rot(double *L, cudaStream_t s) {
+    k_lsmr_rot<<<1, 32, 0, s>>>(L);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsmr_update(float *v, float *x, float *h, float *hbar, size_t n, const double *L,
+                               cudaStream_t s) {
+    k_lsmr_update<<<blocks_for(n), TPB, 0, s>>>(v, x, h, hbar, n, L);
     count_launch();
     return cudaGetLastError();
 }

@@ -84,6 +84,7 @@ def load():
             "tg_cgls": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
             "tg_mlem": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, _DP, _VP],
             "tg_lsqr": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
+            "tg_lsmr": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.c_int, _DP, _VP],
             "tg_asd_pocs": [G, _DP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_PocsParams), _DP, _VP],
             "tg_tv_gradient": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_float, ctypes.c_float, _VP],
             "tg_tv_descent": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_float, ctypes.c_float,
@@ -402,6 +403,18 @@ def lsqr(geo, proj, niter: int, x0=None, resid: bool = False, stream=None):
     x = _x0(geo, proj, x0)
     h, hp = _hist(niter, resid)
     _check("tg_lsqr", load().tg_lsqr(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), int(niter), hp, _stream(proj, stream)))
+    if resid:
+        _sync(proj)
+        return x, h[:niter]
+    return x
+
+
+def lsmr(geo, proj, niter: int, x0=None, resid: bool = False, stream=None):
+    """LSMR; returns x (and ||A x_k - b|| when ``resid``)."""
+    G = _Geo(geo)
+    x = _x0(geo, proj, x0)
+    h, hp = _hist(niter, resid)
+    _check("tg_lsmr", load().tg_lsmr(G.ref, G.ang, G.n, _ptr(proj), _ptr(x), int(niter), hp, _stream(proj, stream)))
     if resid:
         _sync(proj)
         return x, h[:niter]

@@ -151,3 +151,21 @@ def test_lsqr_warm_start_and_zero_data(problem):
     # b = A x0 exactly reached: the recurrence ends and x stays x0
     z = tg.lsqr(g, dev(np.zeros(g.proj_shape)), 3, x0=torch.zeros(g.vol_shape, device="cuda"))
     assert torch.count_nonzero(z) == 0
+
+
+def test_lsmr_20_iterations(problem):
+    g, _, b = problem
+    x, hist = tg.lsmr(g, dev(b), 20, resid=True)
+    xr, hr = oracle.lsmr(g, b, 20)
+    assert rel_l2(host(x), xr) <= RTOL, rel_l2(host(x), xr)
+    np.testing.assert_allclose(hist, hr, rtol=RTOL)
+
+
+def test_lsmr_warm_start_and_zero_data(problem):
+    g, _, b = problem
+    x0 = dev(0.02 * np.random.default_rng(5).random(g.vol_shape))
+    x5 = tg.lsmr(g, dev(b), 5, x0=x0.clone())
+    xr, _ = oracle.lsmr(g, b, 5, x0=host(x0))
+    assert rel_l2(host(x5), xr) <= RTOL
+    z = tg.lsmr(g, dev(np.zeros(g.proj_shape)), 3, x0=torch.zeros(g.vol_shape, device="cuda"))
+    assert torch.count_nonzero(z) == 0
