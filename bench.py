@@ -511,6 +511,85 @@ def run_learned(args):
     return 0
 
 
+def run_solvers(args):
+    """Per-iteration times of the solvers and the extra operators on the
+    512^3 / 720-angle workload (one JSON line): each iterative method runs 1
+    and 2 iterations from x0 (CUDA events); an iteration costs the
+    difference, its set-up (weights, sensitivities, the first projections)
+    the rest."""
+    import math
+
+    import torch
+
+    from paper_2412_10129_gb300 import build, inputs, tg
+    torch.cuda.set_device(0)
+    build.build()
+    tg.load()
+    dev = torch.device("cuda", 0)
+    g, x_np = make_inputs(args.case)
+    b = torch.from_numpy(inputs.poisson_noise(_siddon_gpu(g, x_np, dev), 1e5, seed=2)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    s_interp = tg.count_samples(g, "interp")
+    s_siddon = tg.count_samples(g, "siddon")
+    pairs = int(np.prod(g.vol_shape)) * g.nAngles
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    def iters(name, call, units):
+        t1 = timed(lambda: call(1))
+        t2 = timed(lambda: call(2))
+        it = t2 - t1
+        return {"s_per_iteration": it, "setup_s": t1 - it, "voxel_samples_per_s": units / it if it > 0 else None}
+
+    out = {}
+    v = torch.empty(g.vol_shape, device=dev)
+    ones = lambda: torch.ones(g.vol_shape, device=dev)  # noqa: E731
+    zeros = lambda: torch.zeros(g.vol_shape, device=dev)  # noqa: E731
+    fp_bp = s_interp + pairs
+    out["mlem"] = iters("mlem", lambda n: tg.mlem(g, b, n, x0=ones()), fp_bp)
+    out["osem_20"] = iters("osem", lambda n: tg.osem(g, b, n, blocksize=20, x0=ones()), fp_bp)
+    out["mlem_siddon"] = iters("mlem_siddon", lambda n: tg.mlem(g, b, n, x0=ones(), method="siddon"),
+                               s_siddon + s_siddon)
+    out["os_asd_pocs_20"] = iters("asd", lambda n: tg.asd_pocs(g, b, n, blocksize=20, x0=zeros()), fp_bp)
+    out["lsqr"] = iters("lsqr", lambda n: tg.lsqr(g, b, n, x0=zeros()), fp_bp)
+    out["lsmr"] = iters("lsmr", lambda n: tg.lsmr(g, b, n, x0=zeros()), fp_bp)
+    out["cgls"] = iters("cgls", lambda n: tg.cgls(g, b, n, x0=zeros()), fp_bp)
+    tg.backproject(g, b, "siddon", out=v)
+    t = timed(lambda: tg.backproject(g, b, "siddon", out=v))
+    out["bp_siddon"] = {"s": t, "segments_per_s": s_siddon / t}
+    tv = torch.rand(g.vol_shape, device=dev)
+    tg.tv_descent(tv, 2, 1e-3)
+    out["tv_descent_20_steps"] = {"s": timed(lambda: tg.tv_descent(tv, 20, 1e-3))}
+    filt = torch.empty_like(b)
+    for name in ("ram-lak", "hamming"):
+        tg.fdk_filter(g, b, name, out=filt)
+        out[f"fdk_filter_{name}"] = {"s": timed(lambda: tg.fdk_filter(g, b, name, out=filt))}
+        out[f"fdk_{name}"] = {"s": timed(lambda: tg.fdk(g, b, name, out=v))}
+    # a 200-degree short scan (Parker) and a detector displaced by a quarter
+    # of its width (Wang), 720 views each, same volume and detector
+    n = g.nAngles
+    short = inputs.circular_geometry(g.nVoxel, g.dVoxel, g.nDetector, g.dDetector, n, 1000.0, 1536.0,
+                                     arc=math.radians(200.0) * n / (n - 1))
+    out["fdk_parker_200deg"] = {"s": timed(lambda: tg.fdk(short, b, parker=True, out=v))}
+    off = inputs.circular_geometry(g.nVoxel, g.dVoxel, g.nDetector, g.dDetector, n, 1000.0, 1536.0)
+    off.offDetector[:, 0] = 0.25 * g.nDetector[0] * g.dDetector[0]
+    out["fdk_wang_quarter_offset"] = {"s": timed(lambda: tg.fdk(off, b, wang=True, out=v))}
+    line = {"metric": "solver seconds per iteration at 512^3", "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CASES[args.case][0], "units": "voxel_samples = interpolated samples (or Siddon "
+                                                                   "segments) + voxel-angle pairs per iteration"},
+            "solvers": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _siddon_gpu(g, x_np, dev):
     import torch
 
@@ -525,15 +604,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tg", choices=["tg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="clinical", choices=sorted(CASES) + ["learned"],
+    ap.add_argument("--case", default="clinical", choices=sorted(CASES) + ["learned", "solvers"],
                     help="workload; 'medium' is the half-resolution scan used for profiler captures; 'learned' "
-                         "trains the learned-gradient scheme and times it against CGLS")
+                         "trains the learned-gradient scheme and times it against CGLS; 'solvers' times one "
+                         "iteration of every solver and the extra operators at 512^3")
     ap.add_argument("--pretrain", type=int, default=300, help="learned: 64^3 training batches (2 phantoms each)")
     ap.add_argument("--finetune", type=int, default=40, help="learned: 256^3 training phantoms")
     ap.add_argument("--eval", type=int, default=2, help="learned: held-out phantoms")
     args = ap.parse_args()
     if args.case == "learned":
         return run_learned(args) if args.impl != "reference" else 0
+    if args.case == "solvers":
+        args.case = "clinical"
+        return run_solvers(args) if args.impl != "reference" else 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
