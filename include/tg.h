@@ -374,8 +374,8 @@ tg_status tg_tv_descent(float *vol, const int32_t *dims, int steps, float step, 
                         void *stream);
 
 /* Bytes of device scratch a call would take (op: 0 forward, 1 backproject,
- * 2 fdk, 3 sirt, 4 ossart, 5 cgls, 6 mlem, 7 osem; blocksize only for
- * ossart and osem). */
+ * 2 fdk, 3 sirt, 4 ossart, 5 cgls, 6 mlem, 7 osem, 8 asd_pocs, 9 lsqr,
+ * 10 lsmr; blocksize only for ossart, osem and asd_pocs). */
 tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int batch, int blocksize,
                             size_t *bytes);
 

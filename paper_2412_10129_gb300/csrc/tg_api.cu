@@ -1042,6 +1042,14 @@ tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int bat
             f = ang + 4 * (2 * nray + nvox * nb + nvox) + 96;
             break;
         }
+        case 8: {  // asd_pocs: the OS-SART state plus two volumes
+            if (blocksize <= 0) return TG_ERR_ARG;
+            const size_t nb = (size_t)((nAngles + blocksize - 1) / blocksize);
+            f = ang + 4 * (2 * nray + (nvox > nray ? nvox : nray) + nvox * nb + 2 * nvox) + 128;
+            break;
+        }
+        case 9: f = ang + 4 * (2 * nray + 3 * nvox) + 128; break;   // lsqr
+        case 10: f = ang + 4 * (2 * nray + 4 * nvox) + 192; break;  // lsmr
         default: return TG_ERR_ARG;
     }
     *bytes = f;

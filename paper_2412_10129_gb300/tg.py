@@ -497,7 +497,8 @@ def tv_descent(vol, steps: int, step: float, delta: float = float("inf"), eps: f
 
 
 def workspace_size(geo, op: str, batch: int = 1, blocksize: int = 20) -> int:
-    ops = {"forward": 0, "backproject": 1, "fdk": 2, "sirt": 3, "ossart": 4, "cgls": 5, "mlem": 6, "osem": 7}
+    ops = {"forward": 0, "backproject": 1, "fdk": 2, "sirt": 3, "ossart": 4, "cgls": 5, "mlem": 6, "osem": 7,
+           "asd_pocs": 8, "lsqr": 9, "lsmr": 10}
     G = _Geo(geo)
     out = ctypes.c_size_t(0)
     _check("tg_workspace_size", load().tg_workspace_size(G.ref, G.n, ops[op], int(batch), int(blocksize),

@@ -138,3 +138,44 @@ def test_fdk_weight_options_are_checked_on_the_host(lib):
     assert lib.tg_fdk_ex(O.ref, O.ang, O.n, p.ctypes.data, v.ctypes.data, 0, 2, None) == 2
     with pytest.raises(ValueError):
         tg.fdk(g, p, "gaussian")
+
+
+def test_solver_arguments_are_checked_on_the_host(lib):
+    """Invalid counts, methods, orders and parameters of the EM, Krylov and
+    POCS solvers are refused before any CUDA call; niter = 0 is a no-op."""
+    import math
+    g = _geo()
+    G = tg._Geo(g)
+    p = np.zeros(g.proj_shape, np.float32)
+    v = np.zeros(g.vol_shape, np.float32)
+    P, V = p.ctypes.data, v.ctypes.data
+    assert lib.tg_mlem(G.ref, G.ang, G.n, P, V, -1, 0, None, None) == 1
+    assert lib.tg_mlem(G.ref, G.ang, G.n, P, V, 2, 5, None, None) == 1
+    assert lib.tg_mlem(G.ref, G.ang, G.n, P, V, 0, 0, None, None) == 0
+    assert lib.tg_osem(G.ref, G.ang, G.n, P, V, 2, 0, 0, 0, 0, None, None) == 1
+    assert lib.tg_osem(G.ref, G.ang, G.n, P, V, 2, 2, 7, 0, 0, None, None) == 1
+    assert lib.tg_lsqr(G.ref, G.ang, G.n, P, None, 2, None, None) == 1
+    assert lib.tg_lsmr(G.ref, G.ang, G.n, P, V, -3, None, None) == 1
+    assert lib.tg_lsqr(G.ref, G.ang, G.n, P, V, 0, None, None) == 0
+    good = dict(niter=2, blocksize=1, tv_steps=20, alpha=0.002, alpha_red=0.95, r_max=0.95, data_tol=0.0,
+                beta=1.0, beta_red=0.995, delta=math.inf, eps=1e-8)
+    for bad in (dict(niter=-1), dict(blocksize=0), dict(tv_steps=-2), dict(eps=0.0), dict(delta=-1.0),
+                dict(alpha=math.nan)):
+        prm = tg._PocsParams(**{**good, **bad})
+        assert lib.tg_asd_pocs(G.ref, G.ang, G.n, P, V, ctypes.byref(prm), None, None) == 1, bad
+    assert lib.tg_asd_pocs(G.ref, G.ang, G.n, P, V, None, None, None) == 1
+    zero = tg._PocsParams(**{**good, "niter": 0})
+    assert lib.tg_asd_pocs(G.ref, G.ang, G.n, P, V, ctypes.byref(zero), None, None) == 0
+    dims = (ctypes.c_int32 * 3)(8, 8, 8)
+    assert lib.tg_tv_gradient(V, V, dims, ctypes.c_float(math.inf), ctypes.c_float(1e-8), None) == 1
+    assert lib.tg_tv_descent(None, dims, 3, ctypes.c_float(0.1), ctypes.c_float(math.inf), ctypes.c_float(1e-8),
+                             None) == 1
+    bad_dims = (ctypes.c_int32 * 3)(8, 0, 8)
+    assert lib.tg_tv_descent(V, bad_dims, 3, ctypes.c_float(0.1), ctypes.c_float(math.inf), ctypes.c_float(1e-8),
+                             None) == 1
+
+
+def test_workspace_sizes_of_the_solvers(lib):
+    g = _geo()
+    for op in ("mlem", "osem", "asd_pocs", "lsqr", "lsmr"):
+        assert tg.workspace_size(g, op, blocksize=2) > 4 * int(np.prod(g.vol_shape))
