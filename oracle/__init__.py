@@ -78,6 +78,7 @@ class _Geo(ctypes.Structure):
         ("offDetector", ctypes.POINTER(ctypes.c_double)),
         ("rotDetector", ctypes.POINTER(ctypes.c_double)),
         ("COR", ctypes.POINTER(ctypes.c_double)),
+        ("parallel", ctypes.c_int32),
     ]
 
 
@@ -138,6 +139,7 @@ class _GeoHolder:
         g.dDetector[:] = [float(v) for v in geo.dDetector]
         g.accuracy = float(geo.accuracy)
         g.nAngles = n
+        g.parallel = 1 if getattr(geo, "parallel", False) else 0
         for k, arr in self.arrays.items():
             setattr(g, k, arr.ctypes.data_as(_DP))
         self.g = g

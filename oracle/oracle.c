@@ -28,6 +28,12 @@
  *   projections proj[a][iv][iu] (u = detector column, v = detector row);
  *   per-angle frame: source S, detector centre D, unit pixel axes eu, ev,
  *           unit normal n pointing from the source side to the detector.
+ *   Parallel beam (the synchrotron shapes of Sec. 3): every ray runs along
+ *           the central direction D - S, from S + (P - D) to its pixel
+ *           centre P, so the samples and the ray's length are those of the
+ *           central ray shifted by the pixel's offset; the FDK weights
+ *           become those of parallel FBP (no cosine pre-weight, pitch du,
+ *           no distance weight).
  */
 #include <math.h>
 #include <stdint.h>
@@ -51,6 +57,7 @@ typedef struct {
     const double *offDetector; /* [nAngles][2] mm (u, v) */
     const double *rotDetector; /* [nAngles][3] rad (phi, theta, psi) */
     const double *COR;         /* [nAngles] mm */
+    int32_t parallel;          /* 1: parallel beam (see or_ray_source) */
 } or_geo;
 
 typedef struct {
@@ -146,6 +153,31 @@ void or_pixel_centre(const or_geo *g, const or_frame *f, int iu, int iv, double 
     double su = ((iu + 0.5) - 0.5 * g->nDetector[0]) * g->dDetector[0];
     double sv = ((iv + 0.5) - 0.5 * g->nDetector[1]) * g->dDetector[1];
     for (int i = 0; i < 3; ++i) P[i] = f->D[i] + su * f->eu[i] + sv * f->ev[i];
+}
+
+/* Start of the ray to pixel centre P: the source, or for parallel beam the
+ * source shifted by the pixel's offset from the detector centre. */
+static void or_ray_source(const or_geo *g, const or_frame *f, const double P[3], double Sr[3]) {
+    for (int i = 0; i < 3; ++i) Sr[i] = g->parallel ? f->S[i] + (P[i] - f->D[i]) : f->S[i];
+}
+
+/* Where the line through X along the rays of frame f meets the detector
+ * plane, relative to the detector centre; 0 when X is not in front of the
+ * source (cone beam). */
+static int or_project_point(const or_geo *g, const or_frame *f, const double X[3], double Pc[3]) {
+    double DS[3] = {f->D[0] - f->S[0], f->D[1] - f->S[1], f->D[2] - f->S[2]};
+    if (g->parallel) {
+        double DX[3] = {f->D[0] - X[0], f->D[1] - X[1], f->D[2] - X[2]};
+        double s = dot3(DX, f->n) / dot3(DS, f->n);
+        for (int i = 0; i < 3; ++i) Pc[i] = X[i] + s * DS[i] - f->D[i];
+        return 1;
+    }
+    double XS[3] = {X[0] - f->S[0], X[1] - f->S[1], X[2] - f->S[2]};
+    double den = dot3(XS, f->n);
+    if (den <= 0) return 0;
+    double s = dot3(DS, f->n) / den;
+    for (int i = 0; i < 3; ++i) Pc[i] = f->S[i] + s * XS[i] - f->D[i];
+    return 1;
 }
 
 void or_frames(const or_geo *g, double *out /* [nAngles][15] */) {
@@ -272,7 +304,9 @@ void or_forward_interp(const or_geo *g, const double *vol, double *proj) {
             for (int iu = 0; iu < nu; ++iu) {
                 double P[3];
                 or_pixel_centre(g, &f, iu, iv, P);
-                proj[((long)a * nv + iv) * nu + iu] = ray_interp(g, vol, f.S, P);
+                double Sr[3];
+                or_ray_source(g, &f, P, Sr);
+                proj[((long)a * nv + iv) * nu + iu] = ray_interp(g, vol, Sr, P);
             }
         }
 }
@@ -286,7 +320,9 @@ void or_forward_interp_rays(const or_geo *g, const double *vol, long nrays, cons
         or_frame_for_angle(g, rays[3 * r], &f);
         double P[3];
         or_pixel_centre(g, &f, rays[3 * r + 2], rays[3 * r + 1], P);
-        out[r] = ray_interp(g, vol, f.S, P);
+        double Sr[3];
+        or_ray_source(g, &f, P, Sr);
+        out[r] = ray_interp(g, vol, Sr, P);
     }
 }
 
@@ -322,14 +358,16 @@ void or_backproject_matched(const or_geo *g, const double *proj, double *vol) {
                     if (y == 0.0) continue;
                     double P[3];
                     or_pixel_centre(g, &f, iu, iv, P);
-                    double dir[3] = {P[0] - f.S[0], P[1] - f.S[1], P[2] - f.S[2]};
+                    double Sr[3];
+                    or_ray_source(g, &f, P, Sr);
+                    double dir[3] = {P[0] - Sr[0], P[1] - Sr[1], P[2] - Sr[2]};
                     double L = sqrt(dot3(dir, dir));
                     double dh[3] = {dir[0] / L, dir[1] / L, dir[2] / L};
                     long k0, k1;
-                    if (!sample_range(g, f.S, dh, L, delta, &k0, &k1)) continue;
+                    if (!sample_range(g, Sr, dh, L, delta, &k0, &k1)) continue;
                     for (long k = k0; k <= k1; ++k) {
                         double t = k * delta;
-                        double p[3] = {f.S[0] + t * dh[0], f.S[1] + t * dh[1], f.S[2] + t * dh[2]};
+                        double p[3] = {Sr[0] + t * dh[0], Sr[1] + t * dh[1], Sr[2] + t * dh[2]};
                         if (!inside_closed_box(g, p)) continue;
                         long idx[8];
                         double w[8];
@@ -375,13 +413,8 @@ void or_backproject_matched_voxels(const or_geo *g, const double *proj, long nvo
                 double X[3] = {c[0] + ((q & 1) ? 1 : -1) * g->dVoxel[0],
                                c[1] + ((q & 2) ? 1 : -1) * g->dVoxel[1],
                                c[2] + ((q & 4) ? 1 : -1) * g->dVoxel[2]};
-                double XS[3] = {X[0] - f.S[0], X[1] - f.S[1], X[2] - f.S[2]};
-                double DS[3] = {f.D[0] - f.S[0], f.D[1] - f.S[1], f.D[2] - f.S[2]};
-                double den = dot3(XS, f.n);
-                if (den <= 0) { ok = 0; break; }
-                double s = dot3(DS, f.n) / den;
-                double Pc[3] = {f.S[0] + s * XS[0] - f.D[0], f.S[1] + s * XS[1] - f.D[1],
-                                f.S[2] + s * XS[2] - f.D[2]};
+                double Pc[3];
+                if (!or_project_point(g, &f, X, Pc)) { ok = 0; break; }
                 double fu = dot3(Pc, f.eu) / g->dDetector[0] + 0.5 * nu - 0.5;
                 double fv = dot3(Pc, f.ev) / g->dDetector[1] + 0.5 * nv - 0.5;
                 if (fu < umin) umin = fu;
@@ -401,20 +434,22 @@ void or_backproject_matched_voxels(const or_geo *g, const double *proj, long nvo
                     double y = proj[((long)a * nv + iv) * nu + iu];
                     double P[3];
                     or_pixel_centre(g, &f, iu, iv, P);
-                    double dir[3] = {P[0] - f.S[0], P[1] - f.S[1], P[2] - f.S[2]};
+                    double Sr[3];
+                    or_ray_source(g, &f, P, Sr);
+                    double dir[3] = {P[0] - Sr[0], P[1] - Sr[1], P[2] - Sr[2]};
                     double L = sqrt(dot3(dir, dir));
                     double dh[3] = {dir[0] / L, dir[1] / L, dir[2] / L};
                     long k0, k1;
-                    if (!sample_range(g, f.S, dh, L, delta, &k0, &k1)) continue;
+                    if (!sample_range(g, Sr, dh, L, delta, &k0, &k1)) continue;
                     /* restrict to the samples that can touch this voxel */
-                    double tc = dot3((double[3]){c[0] - f.S[0], c[1] - f.S[1], c[2] - f.S[2]}, dh);
+                    double tc = dot3((double[3]){c[0] - Sr[0], c[1] - Sr[1], c[2] - Sr[2]}, dh);
                     double rad = sqrt(dot3(g->dVoxel, g->dVoxel));
                     long ka = (long)floor((tc - rad) / delta) - 1, kb = (long)ceil((tc + rad) / delta) + 1;
                     if (ka < k0) ka = k0;
                     if (kb > k1) kb = k1;
                     for (long k = ka; k <= kb; ++k) {
                         double t = k * delta;
-                        double p[3] = {f.S[0] + t * dh[0], f.S[1] + t * dh[1], f.S[2] + t * dh[2]};
+                        double p[3] = {Sr[0] + t * dh[0], Sr[1] + t * dh[1], Sr[2] + t * dh[2]};
                         if (!inside_closed_box(g, p)) continue;
                         double w = 1.0;
                         for (int ax = 0; ax < 3; ++ax) {
@@ -493,7 +528,9 @@ void or_forward_siddon(const or_geo *g, const double *vol, double *proj) {
                 for (int iu = 0; iu < nu; ++iu) {
                     double P[3];
                     or_pixel_centre(g, &f, iu, iv, P);
-                    proj[((long)a * nv + iv) * nu + iu] = ray_siddon(g, vol, f.S, P, buf);
+                    double Sr[3];
+                    or_ray_source(g, &f, P, Sr);
+                    proj[((long)a * nv + iv) * nu + iu] = ray_siddon(g, vol, Sr, P, buf);
                 }
             }
         free(buf);
@@ -512,7 +549,9 @@ void or_forward_siddon_rays(const or_geo *g, const double *vol, long nrays, cons
             or_frame_for_angle(g, rays[3 * r], &f);
             double P[3];
             or_pixel_centre(g, &f, rays[3 * r + 2], rays[3 * r + 1], P);
-            out[r] = ray_siddon(g, vol, f.S, P, buf);
+            double Sr[3];
+            or_ray_source(g, &f, P, Sr);
+            out[r] = ray_siddon(g, vol, Sr, P, buf);
         }
         free(buf);
     }
@@ -535,10 +574,12 @@ void or_backproject_siddon(const or_geo *g, const double *proj, double *vol) {
                 if (y == 0.0) continue;
                 double P[3];
                 or_pixel_centre(g, &f, iu, iv, P);
-                double dir[3] = {P[0] - f.S[0], P[1] - f.S[1], P[2] - f.S[2]};
+                double Sr[3];
+                or_ray_source(g, &f, P, Sr);
+                double dir[3] = {P[0] - Sr[0], P[1] - Sr[1], P[2] - Sr[2]};
                 double L = sqrt(dot3(dir, dir));
                 double a0, a1;
-                if (!box_interval(g, f.S, dir, 1.0, &a0, &a1)) continue;
+                if (!box_interval(g, Sr, dir, 1.0, &a0, &a1)) continue;
                 int m = 0;
                 buf[m++] = a0;
                 buf[m++] = a1;
@@ -546,7 +587,7 @@ void or_backproject_siddon(const or_geo *g, const double *proj, double *vol) {
                     if (dir[ax] == 0.0) continue;
                     double h = 0.5 * g->nVoxel[ax] * g->dVoxel[ax];
                     for (int i = 0; i <= g->nVoxel[ax]; ++i) {
-                        double al = (-h + i * g->dVoxel[ax] - f.S[ax]) / dir[ax];
+                        double al = (-h + i * g->dVoxel[ax] - Sr[ax]) / dir[ax];
                         if (al > a0 && al < a1) buf[m++] = al;
                     }
                 }
@@ -558,7 +599,7 @@ void or_backproject_siddon(const or_geo *g, const double *proj, double *vol) {
                     int id[3], ok = 1;
                     for (int ax = 0; ax < 3; ++ax) {
                         double h = 0.5 * g->nVoxel[ax] * g->dVoxel[ax];
-                        id[ax] = (int)floor((f.S[ax] + am * dir[ax] + h) / g->dVoxel[ax]);
+                        id[ax] = (int)floor((Sr[ax] + am * dir[ax] + h) / g->dVoxel[ax]);
                         if (id[ax] < 0 || id[ax] >= g->nVoxel[ax]) ok = 0;
                     }
                     if (!ok) continue;
@@ -591,12 +632,13 @@ void or_fdk_filter(const or_geo *g, const double *proj, double *out) {
             for (int iv = 0; iv < nv; ++iv) {
                 or_frame f;
                 or_frame_for_angle(g, a, &f);
-                double tau = g->dDetector[0] * g->DSO[a] / g->DSD[a];
+                /* parallel beam (FBP): no magnification, no pre-weight */
+                double tau = g->parallel ? g->dDetector[0] : g->dDetector[0] * g->DSO[a] / g->DSD[a];
                 for (int iu = 0; iu < nu; ++iu) {
                     double P[3];
                     or_pixel_centre(g, &f, iu, iv, P);
                     double dir[3] = {P[0] - f.S[0], P[1] - f.S[1], P[2] - f.S[2]};
-                    double w = fabs(dot3(dir, f.n)) / sqrt(dot3(dir, dir));
+                    double w = g->parallel ? 1.0 : fabs(dot3(dir, f.n)) / sqrt(dot3(dir, dir));
                     row[iu] = w * proj[((long)a * nv + iv) * nu + iu];
                 }
                 for (int iu = 0; iu < nu; ++iu) {
@@ -622,16 +664,15 @@ void or_fdk_filter(const or_geo *g, const double *proj, double *out) {
 /* Voxel-driven FDK-weighted backprojection of voxel centre c for angle a:
  * (DSO/L)^2 * bilinear(p, u, v), L = (c - S).n, (u, v) the detector
  * position where the line S -> c meets the detector plane.  Bilinear
- * interpolation is zero outside the detector. */
+ * interpolation is zero outside the detector.  Parallel beam (FBP): the
+ * line through c along the rays, weight 1. */
 static double fdk_bp_one(const or_geo *g, const or_frame *f, const double *p, int a, const double c[3]) {
     int nu = g->nDetector[0], nv = g->nDetector[1];
     double XS[3] = {c[0] - f->S[0], c[1] - f->S[1], c[2] - f->S[2]};
-    double DS[3] = {f->D[0] - f->S[0], f->D[1] - f->S[1], f->D[2] - f->S[2]};
     double L = dot3(XS, f->n);
-    if (L <= 0.0) return 0.0;
-    double s = dot3(DS, f->n) / L;
-    double Pc[3] = {f->S[0] + s * XS[0] - f->D[0], f->S[1] + s * XS[1] - f->D[1],
-                    f->S[2] + s * XS[2] - f->D[2]};
+    if (!g->parallel && L <= 0.0) return 0.0;
+    double Pc[3];
+    or_project_point(g, f, c, Pc);
     double fu = dot3(Pc, f->eu) / g->dDetector[0] + 0.5 * nu - 0.5;
     double fv = dot3(Pc, f->ev) / g->dDetector[1] + 0.5 * nv - 0.5;
     double u0 = floor(fu), v0 = floor(fv);
@@ -645,6 +686,7 @@ static double fdk_bp_one(const or_geo *g, const or_frame *f, const double *p, in
             double w = (du ? au : 1.0 - au) * (dv ? av : 1.0 - av);
             val += w * p[((long)a * nv + iv) * nu + iu];
         }
+    if (g->parallel) return val;
     double r = g->DSO[a] / L;
     return r * r * val;
 }

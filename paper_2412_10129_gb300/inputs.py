@@ -42,6 +42,7 @@ class Geometry:
     rotDetector: np.ndarray  # [nA, 3] rad (phi, theta, psi)
     COR: np.ndarray  # [nA] mm
     accuracy: float = 0.5  # interpolated-projector step, in units of min(dVoxel)
+    parallel: bool = False  # parallel beam: every ray along D - S, through its own pixel
 
     @property
     def nAngles(self) -> int:
@@ -83,6 +84,14 @@ def circular_geometry(nVoxel, dVoxel, nDetector, dDetector, n_angles: int, DSO: 
         angles=ang, DSO=np.full(n, float(DSO)), DSD=np.full(n, float(DSD)),
         offOrigin=np.zeros((n, 3)), offDetector=np.zeros((n, 2)), rotDetector=np.zeros((n, 3)),
         COR=np.zeros(n), accuracy=float(accuracy))
+
+
+def parallel_geometry(nVoxel, dVoxel, nDetector, dDetector, n_angles: int, arc: float = math.pi,
+                      DSO: float = 1000.0, DSD: float = 1536.0) -> Geometry:
+    """Parallel-beam scan (synchrotron shapes): angles start + a * arc / nA;
+    DSO and DSD only place the plane the rays start from and the detector."""
+    g = circular_geometry(nVoxel, dVoxel, nDetector, dDetector, n_angles, DSO, DSD, arc=arc)
+    return dataclasses.replace(g, parallel=True)
 
 
 def jitter_geometry(geo: Geometry, seed: int, det_offset_px: float = 2.0, tilt_deg: float = 0.5,
