@@ -111,6 +111,12 @@ typedef struct {
     const double *offDetector;/* [nAngles][2] (u, v) or NULL (0) */
     const double *rotDetector;/* [nAngles][3] (phi, theta, psi) rad or NULL (0) */
     const double *COR;        /* [nAngles] or NULL (0) */
+    int32_t parallel;         /* 0: cone beam from the source S.  1: parallel beam (the synchrotron
+                                 shapes of Sec. 3): every ray runs along the central direction
+                                 D - S, from S + (P - D) to its pixel centre P (samples and length
+                                 those of the central ray, shifted); FDK becomes parallel FBP
+                                 (pitch du, no cosine or distance weight); Parker / Wang weights
+                                 are TG_ERR_UNSUPPORTED */
 } tg_geometry;
 
 /* Forward projection A x (Eq. 1).  angles: [nAngles][3] ZYZ (z1, y1, z2)
@@ -163,7 +169,8 @@ tg_status tg_gradient(const tg_geometry *geo, const double *angles, int nAngles,
  *   tg_forward_batched:     proj = A_v vol_v for every v;
  *   tg_backproject_batched: vol = A_v^T proj_v;
  *   tg_gradient_batched:    grad (=|+=) A_v^T (A_v vol_v - proj_v), proj may
- *                           be NULL (then A_v^T A_v vol_v). */
+ *                           be NULL (then A_v^T A_v vol_v).
+ * All geometries of a call share one beam mode (else TG_ERR_UNSUPPORTED). */
 tg_status tg_forward_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,
                              const float *vol, float *proj, void *stream);
 tg_status tg_backproject_batched(const tg_geometry *geos, const double *const *angles, const int *nAngles, int nvol,

@@ -44,6 +44,9 @@ definitions written out here are the published methods they name:
   2 (the full-orbit FDK angle weight pi / nAngles halves every line).
 
 The fan angle is gamma = atan2((P - S).e_u, |(P - S).n|) for pixel centre P.
+
+Parallel beam (geo.parallel): no cosine pre-weight and the pitch du (parallel
+FBP); Parker and Wang weights are not defined for it here.
 """
 from __future__ import annotations
 
@@ -173,6 +176,10 @@ def pre_weights(geo, parker: bool = False, wang: bool = False) -> np.ndarray:
     weights, [nAngles, nv, nu]."""
     n = int(geo.nAngles)
     nu, nv = (int(v) for v in geo.nDetector)
+    if getattr(geo, "parallel", False):
+        if parker or wang:
+            raise ValueError("Parker and Wang weights are defined for cone beams only")
+        return np.ones((n, nv, nu))
     out = np.zeros((n, nv, nu))
     if parker:
         beta, _, Delta = parker_scan(geo)
@@ -193,8 +200,11 @@ def fdk_filter(geo, proj, filter: str = "ram-lak", parker: bool = False, wang: b
     p = np.asarray(proj, dtype=np.float64).reshape(geo.proj_shape)
     if parker and wang:
         raise ValueError("Parker and Wang weights are not combined")
-    tau = np.asarray(geo.dDetector[0] * np.asarray(geo.DSO, np.float64).reshape(-1)
-                     / np.asarray(geo.DSD, np.float64).reshape(-1))
+    if getattr(geo, "parallel", False):
+        tau = np.full(int(geo.nAngles), float(geo.dDetector[0]))
+    else:
+        tau = np.asarray(geo.dDetector[0] * np.asarray(geo.DSO, np.float64).reshape(-1)
+                         / np.asarray(geo.DSD, np.float64).reshape(-1))
     rows = p * pre_weights(geo, parker, wang)
     return filter_rows(rows, tau[:, None], filter)
 

@@ -560,6 +560,8 @@ tg_status ragged_setup(Call &c, const tg_geometry *geos, const double *const *an
     for (int v = 0; v < nvol; ++v) {
         tg_status st = check_common(&geos[v], angles[v], nAngles[v]);
         if (st != TG_OK) return st;
+        // one launch serves one beam mode
+        if ((geos[v].parallel != 0) != (geos[0].parallel != 0)) return TG_ERR_UNSUPPORTED;
         r.angle0.push_back((int)h.size());
         h.resize(h.size() + (size_t)nAngles[v]);
         if (nAngles[v] > 0) build_angles(&geos[v], angles[v], nAngles[v], h.data() + r.angle0.back());
@@ -668,6 +670,7 @@ static tg_status check_fdk(const tg_geometry *geo, const double *angles, int nAn
     if (filter < TG_RAMLAK || filter > TG_HANN) return TG_ERR_ARG;
     if (weights & ~(TG_FDK_PARKER | TG_FDK_WANG)) return TG_ERR_ARG;
     if (weights == (TG_FDK_PARKER | TG_FDK_WANG)) return TG_ERR_UNSUPPORTED;
+    if (weights && geo->parallel) return TG_ERR_UNSUPPORTED;
     if (fdk_filter_smem(geo->nDetector[0], filter) > 227 * 1024) return TG_ERR_UNSUPPORTED;
     if (weights && nAngles > 0) {
         std::vector<FdkAngle> h((size_t)nAngles);

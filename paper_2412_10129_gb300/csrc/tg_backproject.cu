@@ -111,8 +111,9 @@ __global__ void k_absmax(const float *__restrict__ y, size_t n, unsigned int *ou
 // ---- matched transpose ------------------------------------------------------
 // Out of line: the membership walk is only taken on boundary bricks and
 // would otherwise crowd the registers of the scatter loop.
+template <bool PAR>
 __device__ __noinline__ bool ray_setup_outlined(const Angle &A, const Grid &g, int iu, int iv, Ray &r) {
-    return ray_setup(A, g, iu, iv, r);
+    return ray_setup<PAR>(A, g, iu, iv, r);
 }
 
 constexpr int BX = 32, BY = 32, BZ = 16;              // owned voxels per brick
@@ -150,7 +151,7 @@ static_assert(MATCHED_SMEM <= 232448, "shared memory of one CTA");
 
 // Sets up ray (iu, iv) against the region [lo, hi] and fills rec; false
 // when it has no sample there or carries y = 0 (it would add nothing).
-template <bool F32>
+template <bool F32, bool PAR>
 __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const float *pa, int iu, int iv, bool edge,
                                            float lox, float loy, float loz, float hix, float hiy, float hiz,
                                            float ybig, float scale, float scale_f, RayRec &rec) {
@@ -159,12 +160,12 @@ __device__ __forceinline__ bool region_ray(const Angle &A, const Grid &g, const 
     Ray r;
     int kb0 = 0, kb1 = 0x7fffffff;
     if (edge) {
-        if (!ray_setup_outlined(A, g, iu, iv, r)) return false;
+        if (!ray_setup_outlined<PAR>(A, g, iu, iv, r)) return false;
         kb0 = r.k0;
         kb1 = r.k1;
     } else {
         float Ld;
-        ray_frame(A, g, iu, iv, r, Ld);  // the forward kernel's sample positions
+        ray_frame<PAR>(A, g, iu, iv, r, Ld);  // the forward kernel's sample positions
     }
     float klo = (float)kb0, khi = (float)kb1;
     const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
@@ -241,7 +242,7 @@ __device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float 
 // One brick (bx, by, bz) of one volume: pb are the volume's projections,
 // vb its output (and the SIRT weight's) voxels, gmax its max |y|; the
 // epilogue writes vb directly and adds the FP64 norm to ep.norm[0].
-template <int MODE, bool F32>
+template <int MODE, bool F32, bool PAR>
 __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, float *__restrict__ vb,
                                                  const Angle *__restrict__ angles, const Grid &g, const BpEpilogue &ep,
                                                  float gmax, int bx, int by, int bz) {
@@ -327,7 +328,7 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
                         const int iu = u0 + (tile % ntu) * 32 + (slot & 7) * 4 + (ph & 3);
                         const int iv = v0 + (tile / ntu) * 16 + (slot >> 3) * 4 + (ph >> 2);
                         if (iu <= u1 && iv <= v1)
-                            keep = region_ray<F32>(A, g, pa, iu, iv, edge, lox, loy, loz, hix, hiy, hiz, ybig,
+                            keep = region_ray<F32, PAR>(A, g, pa, iu, iv, edge, lox, loy, loz, hix, hiy, hiz, ybig,
                                                    scale, scale_f, rec);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -358,7 +359,7 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
                                 const RayRec rr = rays[idx];
                                 Ray q;
                                 float Ld;
-                                ray_frame(A, g, (int)(rr.iuv & 0xffffu), (int)(rr.iuv >> 16), q, Ld);
+                                ray_frame<PAR>(A, g, (int)(rr.iuv & 0xffffu), (int)(rr.iuv >> 16), q, Ld);
                                 gx = q.gx;
                                 gy = q.gy;
                                 gz = q.gz;
@@ -423,7 +424,7 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
 }
 
-template <int MODE, bool F32>
+template <int MODE, bool F32, bool PAR>
 __global__ void __launch_bounds__(MT, 1)
     k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
                  BpEpilogue ep, int nbx, int nby) {
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(MT, 1)
     BpEpilogue e = ep;
     if (e.norm) e.norm += b;
     const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-    bp_matched_brick<MODE, F32>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
+    bp_matched_brick<MODE, F32, PAR>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
                                 __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
 }
 
@@ -448,7 +449,7 @@ struct BpRagged {
     Grid g[BPR_MAXV];
 };
 
-template <int MODE, bool F32>
+template <int MODE, bool F32, bool PAR>
 __global__ void __launch_bounds__(MT, 1)
     k_bp_matched_ragged(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles,
                         const __grid_constant__ BpRagged tab, BpEpilogue ep) {
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(MT, 1)
     BpEpilogue e = ep;
     e.scale = tab.scale[v];
     if (e.norm) e.norm += v;
-    bp_matched_brick<MODE, F32>(proj + tab.p0[v], vol + tab.v0[v], angles + tab.a0[v], tab.g[v], e,
+    bp_matched_brick<MODE, F32, PAR>(proj + tab.p0[v], vol + tab.v0[v], angles + tab.a0[v], tab.g[v], e,
                                 __uint_as_float(ep.absmax[v]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
 }
 
@@ -544,14 +545,21 @@ __global__ void __launch_bounds__(256) k_bp_fdk(const float *__restrict__ proj, 
     }
 }
 
+template <int MODE, bool F32, bool PAR>
+cudaError_t launch_matched_t(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
+                             const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_bp_matched<MODE, F32, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         MATCHED_SMEM);
+    if (e != cudaSuccess) return e;
+    k_bp_matched<MODE, F32, PAR><<<grid, MT, MATCHED_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
+    return cudaSuccess;
+}
+
 template <int MODE, bool F32>
 cudaError_t launch_matched(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
                            const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_bp_matched<MODE, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         MATCHED_SMEM);
-    if (e != cudaSuccess) return e;
-    k_bp_matched<MODE, F32><<<grid, MT, MATCHED_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
-    return cudaSuccess;
+    return g.parallel ? launch_matched_t<MODE, F32, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                      : launch_matched_t<MODE, F32, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
 }
 
 }  // namespace
@@ -650,6 +658,7 @@ cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int n
         for (int k = 0; k < n; ++k) {
             const Grid &g = gs[v0 + k];
             if (!(g.wbound > 0.f)) return cudaErrorInvalidValue;
+            if (g.parallel != gs[0].parallel) return cudaErrorInvalidValue;  // one beam mode per call
             const int nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY, nbz = (g.nz + BZ - 1) / BZ;
             tab.g[k] = g;
             tab.nbx[k] = nbx;
@@ -677,16 +686,19 @@ cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int n
             count_launch();
         }
         if (blocks > 0) {
-#define TG_BPR(M, F)                                                                                              \
+#define TG_BPR(M, F, P)                                                                                           \
     do {                                                                                                          \
-        e = cudaFuncSetAttribute(k_bp_matched_ragged<M, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+        e = cudaFuncSetAttribute(k_bp_matched_ragged<M, F, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                  MATCHED_SMEM);                                                                   \
         if (e != cudaSuccess) return e;                                                                           \
-        k_bp_matched_ragged<M, F><<<(unsigned)blocks, MT, MATCHED_SMEM, s>>>(proj + pix, vol + vox, d_angles, tab, \
-                                                                            ep);                                 \
+        k_bp_matched_ragged<M, F, P><<<(unsigned)blocks, MT, MATCHED_SMEM, s>>>(proj + pix, vol + vox, d_angles, \
+                                                                               tab, ep);                         \
     } while (0)
-            if (mode == BP_STORE) TG_BPR(BP_STORE, false);
-            else if (mode == BP_SIRT) TG_BPR(BP_SIRT, false);
+            const bool par = gs[0].parallel != 0;
+            if (mode == BP_STORE && !par) TG_BPR(BP_STORE, false, false);
+            else if (mode == BP_STORE) TG_BPR(BP_STORE, false, true);
+            else if (mode == BP_SIRT && !par) TG_BPR(BP_SIRT, false, false);
+            else if (mode == BP_SIRT) TG_BPR(BP_SIRT, false, true);
             else return cudaErrorInvalidValue;
 #undef TG_BPR
             count_launch();

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) k_fdk_rows(const float *__restrict__ proj
         float val = 0.f;
         if (i >= 0 && i < nu) {
             const float u = fmaf((float)i, g.du, F.u00);
-            float w = F.depth * rsqrtf(fmaf(u, u, dv2));
+            float w = F.depth > 0.f ? F.depth * rsqrtf(fmaf(u, u, dv2)) : 1.f;  // depth 0: parallel FBP
             if (weights & TG_FDK_PARKER) w *= parker_weight(F.beta, atan2f(u, F.depth), Delta);
             if (weights & TG_FDK_WANG) {
                 const float t = fminf(fmaxf(F.wside * u, -F.wu0), F.wu0);

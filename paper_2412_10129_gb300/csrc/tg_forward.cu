@@ -62,8 +62,10 @@ __device__ __forceinline__ void fp_epilogue(float sum, bool valid, size_t pidx, 
     }
 }
 
-// Interpolated projector: b_i = delta * sum_k trilinear(x, p_k).
-template <int MODE>
+// Interpolated projector: b_i = delta * sum_k trilinear(x, p_k).  PAR:
+// parallel beam (every kernel below that sets up rays takes it as a
+// template parameter).
+template <int MODE, bool PAR>
 __global__ void __launch_bounds__(256) k_fp_interp(const float *__restrict__ vol, float *__restrict__ proj,
                                                    const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
                                                    int nvb) {
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(256) k_fp_interp(const float *__restrict__ vol
     const Angle &A = angles[a];
     Ray r;
     bool has = false;
-    if (valid) has = ray_setup(A, g, iu, iv, r);
+    if (valid) has = ray_setup<PAR>(A, g, iu, iv, r);
     const int k0 = has ? r.k0 : INT_MAX, k1 = has ? r.k1 : INT_MIN;
     // Lanes step through the global sample index together, so that at any
     // iteration the warp's samples lie at one distance from the source.
@@ -133,7 +135,7 @@ __device__ __forceinline__ float4 gather4(cudaTextureObject_t t, int layer, floa
 // block (ub, a, vb) of volume layers lz0 .. lz0 + nz - 1.  PADDED: the
 // array is wider than this volume (ragged batches), so corners past its own
 // nx, ny are zeroed here instead of by the texture border.
-template <int MODE, bool PADDED>
+template <int MODE, bool PADDED, bool PAR>
 __device__ __forceinline__ void fp_interp_tex_rays(cudaTextureObject_t tex, float *__restrict__ proj,
                                                    const Angle *__restrict__ angles, const Grid &g,
                                                    const FpEpilogue &ep, int ub, int a, int vb, int lz0,
@@ -148,7 +150,7 @@ __device__ __forceinline__ void fp_interp_tex_rays(cudaTextureObject_t tex, floa
     const Angle &A = angles[a];
     Ray r;
     bool has = false;
-    if (valid) has = ray_setup(A, g, iu, iv, r);
+    if (valid) has = ray_setup<PAR>(A, g, iu, iv, r);
     const int k0 = has ? r.k0 : INT_MAX, k1 = has ? r.k1 : INT_MIN;
     const int kw0 = __reduce_min_sync(0xffffffffu, k0);
     const int kw1 = __reduce_max_sync(0xffffffffu, k1);
@@ -188,12 +190,12 @@ __device__ __forceinline__ void fp_interp_tex_rays(cudaTextureObject_t tex, floa
     fp_epilogue<MODE>(__fmul_rn(acc, g.delta), valid, pbase + widx, widx, ep, proj, b);  // rounded product: no FMA into b - A x
 }
 
-template <int MODE>
+template <int MODE, bool PAR>
 __global__ void __launch_bounds__(256) k_fp_interp_tex(cudaTextureObject_t tex, float *__restrict__ proj,
                                                        const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
                                                        int nvb, int b0) {
     const int vb = blockIdx.z % nvb, bl = blockIdx.z / nvb, b = b0 + bl;
-    fp_interp_tex_rays<MODE, false>(tex, proj, angles, g, ep, blockIdx.x, blockIdx.y, vb, bl * g.nz,
+    fp_interp_tex_rays<MODE, false, PAR>(tex, proj, angles, g, ep, blockIdx.x, blockIdx.y, vb, bl * g.nz,
                                     (size_t)b * g.nA * g.nv * g.nu, b);
 }
 
@@ -212,7 +214,7 @@ struct FpRagged {
     Grid g[FPR_MAXV];
 };
 
-template <int MODE>
+template <int MODE, bool PAR>
 __global__ void __launch_bounds__(256) k_fp_interp_tex_ragged(cudaTextureObject_t tex, float *__restrict__ proj,
                                                               const Angle *__restrict__ angles,
                                                               const __grid_constant__ FpRagged tab, FpEpilogue ep) {
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(256) k_fp_interp_tex_ragged(cudaTextureObject_
     const Grid &g = tab.g[v];
     const int local = blk - tab.blk0[v];
     const int ub = local % tab.nub[v], a = (local / tab.nub[v]) % g.nA, vb = local / (tab.nub[v] * g.nA);
-    fp_interp_tex_rays<MODE, true>(tex, proj, angles + tab.a0[v], g, ep, ub, a, vb, tab.lz0[v],
+    fp_interp_tex_rays<MODE, true, PAR>(tex, proj, angles + tab.a0[v], g, ep, ub, a, vb, tab.lz0[v],
                                    (size_t)tab.p0[v], v);
 }
 
@@ -308,20 +310,47 @@ cudaError_t copy_to_texture(const TexCache &c, const float *vol, const Grid &g, 
 // accumulated.  The walk calls visit(cell index, segment length) for every
 // cell segment inside the volume: the projector sums length * x, its
 // transpose scatters length * y, the counter counts.
-template <class Visit>
+template <bool PAR, class Visit>
 __device__ __forceinline__ void siddon_walk(const Angle &A, const Grid &g, int iu, int iv, Visit &visit) {
     const float fu = (float)iu, fv = (float)iv;
-    const float dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
-    const float dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
-    const float dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
+    // parallel beam: one direction, the start moves with the pixel
+    float dx, dy, dz;
+    if constexpr (PAR) {
+        dx = A.dir0[0];
+        dy = A.dir0[1];
+        dz = A.dir0[2];
+    } else {
+        dx = fmaf(fv, A.Vf[0], fmaf(fu, A.Uf[0], A.dir0[0]));
+        dy = fmaf(fv, A.Vf[1], fmaf(fu, A.Uf[1], A.dir0[1]));
+        dz = fmaf(fv, A.Vf[2], fmaf(fu, A.Uf[2], A.dir0[2]));
+    }
     const float ss = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float invL = rsqrtf(ss);
     const float L = ss * invL;
     // h = index + 1/2: cell i spans [i, i + 1); the box is [0, n] per axis.
-    const float S[3] = {A.Sg[0] + 0.5f, A.Sg[1] + 0.5f, A.Sg[2] + 0.5f};
+    // The walk measures t (mm) from S; the segment is t in [0, L].  A
+    // parallel ray is measured from its point level with the volume centre
+    // instead (small coordinates), so its segment is [-t0, L - t0].
+    // A parallel ray's start is double-float (Sl the low parts): with rays
+    // almost parallel to a grid plane, a lateral error of one FP32 ulp would
+    // move that plane's crossing along the ray by ulp / slope.
+    float S[3] = {A.Sg[0] + 0.5f, A.Sg[1] + 0.5f, A.Sg[2] + 0.5f};
+    float Sl[3] = {0.f, 0.f, 0.f};
+    float tin = 0.f, tout = L;
+    if constexpr (PAR) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float uh, ul, vh, vl, th, tl;
+            df_mulf(A.Uih[a], A.Uil[a], fu, uh, ul);
+            df_mulf(A.Vih[a], A.Vil[a], fv, vh, vl);
+            df_add(A.Cgh[a], A.Cgl[a], uh, ul, th, tl);
+            df_add(th, tl, vh, vl, S[a], Sl[a]);
+        }
+        tin = -A.t0;
+        tout = L - A.t0;
+    }
     const float D[3] = {dx * invL * g.idx, dy * invL * g.idy, dz * invL * g.idz};  // per mm
     const int n[3] = {g.nx, g.ny, g.nz};
-    float tin = 0.f, tout = L;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (D[a] != 0.f) {
@@ -338,17 +367,29 @@ __device__ __forceinline__ void siddon_walk(const Angle &A, const Grid &g, int i
     float t0[3], dt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float h = fmaf(tin, D[a], S[a]);
+        float h, lo = 0.f;  // entry point h (+ lo, parallel beam)
+        if constexpr (PAR) {
+            lo = fmaf(tin, D[a], Sl[a]);
+            h = S[a] + lo;
+        } else {
+            h = fmaf(tin, D[a], S[a]);
+        }
         if (D[a] > 0.f) {
             c[a] = min(max((int)floorf(h), 0), n[a] - 1);
             st[a] = 1;
             dt[a] = __frcp_rn(D[a]);
-            t0[a] = ((float)(c[a] + 1) - h) * dt[a];
+            if constexpr (PAR)
+                t0[a] = (((float)(c[a] + 1) - S[a]) - lo) * dt[a];
+            else
+                t0[a] = ((float)(c[a] + 1) - h) * dt[a];
         } else if (D[a] < 0.f) {
             c[a] = min(max((int)ceilf(h) - 1, 0), n[a] - 1);
             st[a] = -1;
             dt[a] = -__frcp_rn(D[a]);
-            t0[a] = (h - (float)c[a]) * dt[a];
+            if constexpr (PAR)
+                t0[a] = ((S[a] - (float)c[a]) + lo) * dt[a];
+            else
+                t0[a] = (h - (float)c[a]) * dt[a];
         } else {
             c[a] = (int)floorf(h);
             st[a] = 0;
@@ -394,20 +435,20 @@ struct SiddonScatter {
 
 // With COUNT the walk returns the number of cell segments it visits instead
 // of the line integral (the unit of work the benchmark reports).
-template <bool COUNT = false>
+template <bool COUNT = false, bool PAR = false>
 __device__ __forceinline__ float siddon_ray(const float *__restrict__ v, const Angle &A, const Grid &g,
                                             int iu, int iv) {
     if (COUNT) {
         SiddonCount c{0.f};
-        siddon_walk(A, g, iu, iv, c);
+        siddon_walk<PAR>(A, g, iu, iv, c);
         return c.acc;
     }
     SiddonSum f{v, 0.f};
-    siddon_walk(A, g, iu, iv, f);
+    siddon_walk<PAR>(A, g, iu, iv, f);
     return f.acc;
 }
 
-template <int MODE>
+template <int MODE, bool PAR>
 __global__ void __launch_bounds__(256) k_fp_siddon(const float *__restrict__ vol, float *__restrict__ proj,
                                                    const Angle *__restrict__ angles, Grid g, FpEpilogue ep,
                                                    int nvb) {
@@ -417,7 +458,7 @@ __global__ void __launch_bounds__(256) k_fp_siddon(const float *__restrict__ vol
     pixel_of(iu, iv, vb);
     const bool valid = iu < g.nu && iv < g.nv;
     const float *v = vol + (size_t)b * (size_t)g.nx * g.ny * g.nz;
-    const float sum = valid ? siddon_ray(v, angles[a], g, iu, iv) : 0.f;
+    const float sum = valid ? siddon_ray<false, PAR>(v, angles[a], g, iu, iv) : 0.f;
     const size_t widx = ((size_t)a * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
     const size_t pidx = (size_t)b * g.nA * g.nv * g.nu + widx;
     fp_epilogue<MODE>(sum, valid, pidx, widx, ep, proj, b);
@@ -427,6 +468,7 @@ __global__ void __launch_bounds__(256) k_fp_siddon(const float *__restrict__ vol
 // scale * y_i.  One thread per ray walks the same cells with the same
 // lengths as the projector and adds each contribution to global memory
 // (FP32 reductions in L2, so the summation order varies between runs).
+template <bool PAR>
 __global__ void __launch_bounds__(256) k_bp_siddon_scatter(const float *__restrict__ proj, float *__restrict__ out,
                                                            const Angle *__restrict__ angles, Grid g, float scale,
                                                            int nvb) {
@@ -438,7 +480,7 @@ __global__ void __launch_bounds__(256) k_bp_siddon_scatter(const float *__restri
     const float y = scale * proj[(((size_t)b * g.nA + a) * g.nv + iv) * g.nu + iu];
     if (y == 0.f) return;
     SiddonScatter f{out + (size_t)b * g.nx * g.ny * g.nz, y};
-    siddon_walk(angles[a], g, iu, iv, f);
+    siddon_walk<PAR>(angles[a], g, iu, iv, f);
 }
 
 // Units of work of a forward projection: kept samples per ray (TG_INTERP)
@@ -452,9 +494,12 @@ __global__ void __launch_bounds__(256) k_count(int method, const Angle *__restri
     if (iu < g.nu && iv < g.nv) {
         if (method == TG_INTERP) {
             Ray r;
-            if (ray_setup(angles[a], g, iu, iv, r)) n = (unsigned long long)(r.k1 - r.k0 + 1);
+            const bool has = g.parallel ? ray_setup<true>(angles[a], g, iu, iv, r)
+                                        : ray_setup<false>(angles[a], g, iu, iv, r);
+            if (has) n = (unsigned long long)(r.k1 - r.k0 + 1);
         } else {
-            n = (unsigned long long)siddon_ray<true>(nullptr, angles[a], g, iu, iv);
+            n = (unsigned long long)(g.parallel ? siddon_ray<true, true>(nullptr, angles[a], g, iu, iv)
+                                                : siddon_ray<true, false>(nullptr, angles[a], g, iu, iv));
         }
     }
 #pragma unroll
@@ -487,6 +532,7 @@ cudaError_t launch_forward_ragged(const Grid *gs, int nvol, const int *angle0, c
         while (v0 + n < nvol && n < FPR_MAXV && layers + gs[v0 + n].nz <= 2048) {
             const Grid &g = gs[v0 + n];
             if (!texture_fits(g)) return cudaErrorInvalidValue;
+            if (g.parallel != gs[0].parallel) return cudaErrorInvalidValue;  // one beam mode per call
             const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
             tab.g[n] = g;
             tab.nub[n] = nub;
@@ -519,12 +565,19 @@ cudaError_t launch_forward_ragged(const Grid *gs, int nvol, const int *angle0, c
         FpEpilogue e1 = ep;
         if (e1.b) e1.b += pix;
         if (blocks > 0) {
-            switch (mode) {
-                case FP_STORE:
-                    k_fp_interp_tex_ragged<FP_STORE><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
+            const bool par = gs[0].parallel != 0;
+            switch (mode * 2 + (par ? 1 : 0)) {
+                case FP_STORE * 2:
+                    k_fp_interp_tex_ragged<FP_STORE, false><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
                     break;
-                case FP_RESID_W:
-                    k_fp_interp_tex_ragged<FP_RESID_W><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
+                case FP_STORE * 2 + 1:
+                    k_fp_interp_tex_ragged<FP_STORE, true><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
+                    break;
+                case FP_RESID_W * 2:
+                    k_fp_interp_tex_ragged<FP_RESID_W, false><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
+                    break;
+                case FP_RESID_W * 2 + 1:
+                    k_fp_interp_tex_ragged<FP_RESID_W, true><<<(unsigned)blocks, 256, 0, s>>>(tc.tex, proj + pix, d_angles, tab, e1);
                     break;
                 default: return cudaErrorInvalidValue;
             }
@@ -544,12 +597,16 @@ cudaError_t launch_siddon_scatter(const Grid &g, const Angle *d_angles, const fl
     if (g.nA == 0 || batch == 0) return cudaSuccess;
     const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
     if ((long long)nvb * batch > 65535 || g.nA > 65535) return cudaErrorInvalidConfiguration;
-    k_bp_siddon_scatter<<<dim3(nub, g.nA, nvb * batch), 256, 0, s>>>(proj, out, d_angles, g, scale, nvb);
+    if (g.parallel)
+        k_bp_siddon_scatter<true><<<dim3(nub, g.nA, nvb * batch), 256, 0, s>>>(proj, out, d_angles, g, scale, nvb);
+    else
+        k_bp_siddon_scatter<false><<<dim3(nub, g.nA, nvb * batch), 256, 0, s>>>(proj, out, d_angles, g, scale, nvb);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol, float *proj,
+template <bool PAR>
+cudaError_t launch_forward_t(int method, const Grid &g, const Angle *d_angles, const float *vol, float *proj,
                            int batch, int mode, const FpEpilogue &ep, cudaStream_t s) {
     if (g.nA == 0 || batch == 0) return cudaSuccess;
     const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
@@ -575,11 +632,11 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
             if (e != cudaSuccess) return e;
             dim3 grid1(nub, g.nA, nvb * nb);
             switch (mode) {
-                case FP_STORE: k_fp_interp_tex<FP_STORE><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
-                case FP_RESID_W: k_fp_interp_tex<FP_RESID_W><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
-                case FP_STORE_NORM: k_fp_interp_tex<FP_STORE_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
-                case FP_RESID_NORM: k_fp_interp_tex<FP_RESID_NORM><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
-                case FP_RATIO: k_fp_interp_tex<FP_RATIO><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_STORE: k_fp_interp_tex<FP_STORE, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_RESID_W: k_fp_interp_tex<FP_RESID_W, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_STORE_NORM: k_fp_interp_tex<FP_STORE_NORM, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_RESID_NORM: k_fp_interp_tex<FP_RESID_NORM, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
+                case FP_RATIO: k_fp_interp_tex<FP_RATIO, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
                 default: return cudaErrorInvalidValue;
             }
             count_launch();
@@ -590,20 +647,20 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
     } else if (method == TG_INTERP) {
         // volumes beyond the layered-texture limits read global memory
         switch (mode) {
-            case FP_STORE: k_fp_interp<FP_STORE><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_RESID_W: k_fp_interp<FP_RESID_W><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_STORE_NORM: k_fp_interp<FP_STORE_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_RESID_NORM: k_fp_interp<FP_RESID_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_RATIO: k_fp_interp<FP_RATIO><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_STORE: k_fp_interp<FP_STORE, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_W: k_fp_interp<FP_RESID_W, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_STORE_NORM: k_fp_interp<FP_STORE_NORM, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_NORM: k_fp_interp<FP_RESID_NORM, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RATIO: k_fp_interp<FP_RATIO, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             default: return cudaErrorInvalidValue;
         }
     } else if (method == TG_SIDDON) {
         switch (mode) {
-            case FP_STORE: k_fp_siddon<FP_STORE><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_RESID_W: k_fp_siddon<FP_RESID_W><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_STORE_NORM: k_fp_siddon<FP_STORE_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_RESID_NORM: k_fp_siddon<FP_RESID_NORM><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
-            case FP_RATIO: k_fp_siddon<FP_RATIO><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_STORE: k_fp_siddon<FP_STORE, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_W: k_fp_siddon<FP_RESID_W, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_STORE_NORM: k_fp_siddon<FP_STORE_NORM, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RESID_NORM: k_fp_siddon<FP_RESID_NORM, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
+            case FP_RATIO: k_fp_siddon<FP_RATIO, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
@@ -611,6 +668,12 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
     }
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol, float *proj,
+                           int batch, int mode, const FpEpilogue &ep, cudaStream_t s) {
+    return g.parallel ? launch_forward_t<true>(method, g, d_angles, vol, proj, batch, mode, ep, s)
+                      : launch_forward_t<false>(method, g, d_angles, vol, proj, batch, mode, ep, s);
 }
 
 }  // namespace tg

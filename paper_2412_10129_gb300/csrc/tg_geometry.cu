@@ -177,6 +177,49 @@ tg_status build_angles(const tg_geometry *g, const double *angles, int nAngles, 
         const double DSO = at(g->DSO, a, g->DSO0), DSD = at(g->DSD, a, g->DSD0);
         A.DSO = (float)DSO;
         A.tau = (float)(du * DSO / DSD);
+        if (g->parallel) {
+            // rays along r = D - S; pixel (iu, iv)'s ray starts at
+            // S + (P - D) = S00 + iu U + iv V
+            double S00[3];
+            for (int i = 0; i < 3; ++i) S00[i] = f.S[i] + su0 * f.eu[i] + sv0 * f.ev[i];
+            A.par = 1.f;
+            {
+                // the point of pixel (0, 0)'s ray level with the volume centre
+                const double L = sqrt(dot(DS, DS));
+                const double t0 = -(S00[0] * DS[0] + S00[1] * DS[1] + S00[2] * DS[2]) / L;
+                A.t0 = (float)t0;
+                for (int i = 0; i < 3; ++i)
+                    split((S00[i] + t0 * DS[i] / L) / g->dVoxel[i] + 0.5 * g->nVoxel[i], A.Cgh[i], A.Cgl[i]);
+            }
+            for (int i = 0; i < 3; ++i) {
+                A.S[i] = S00[i];
+                A.Sg[i] = (float)(S00[i] / g->dVoxel[i] + 0.5 * g->nVoxel[i] - 0.5);
+                split(S00[i] / g->dVoxel[i] + 0.5 * g->nVoxel[i] - 0.5, A.Shi[i], A.Slo[i]);
+                A.dir0[i] = (float)DS[i];
+                split(DS[i], A.D0hi[i], A.D0lo[i]);
+                split(A.U[i] / g->dVoxel[i], A.Uih[i], A.Uil[i]);
+                split(A.V[i] / g->dVoxel[i], A.Vih[i], A.Vil[i]);
+            }
+            // Parallel projection of a point c onto the detector:
+            // fu = c.eu' / du + cu with eu' = eu - n (r.eu) / (r.n) and
+            // cu = (D.n (r.eu) / (r.n) - D.eu) / du + nu/2 - 1/2 (same for v);
+            // n = 0 and Sn = -1 make the kernels' depth L = 1.
+            const double rn = DSn, reu = dot(DS, f.eu), rev = dot(DS, f.ev), Dn = dot(f.D, f.n);
+            for (int i = 0; i < 3; ++i) {
+                A.eu[i] = (float)(f.eu[i] - f.n[i] * reu / rn);
+                A.ev[i] = (float)(f.ev[i] - f.n[i] * rev / rn);
+                A.n[i] = 0.f;
+            }
+            A.Sn = -1.f;
+            A.Seu = 0.f;
+            A.Sev = 0.f;
+            A.Ku = (float)(1.0 / du);
+            A.Kv = (float)(1.0 / dv);
+            A.cu = (float)((Dn * reu / rn - dot(f.D, f.eu)) / du + 0.5 * nu - 0.5);
+            A.cv = (float)((Dn * rev / rn - dot(f.D, f.ev)) / dv + 0.5 * nv - 0.5);
+            A.DSO = 1.f;
+            A.tau = (float)du;
+        }
     }
     return TG_OK;
 }
@@ -208,7 +251,7 @@ tg_status build_fdk_angles(const tg_geometry *g, const double *angles, int nAngl
             DS[i] = f.D[i] - f.S[i];
             P00S[i] = DS[i] + (0.5 - 0.5 * nu) * du * f.eu[i] + (0.5 - 0.5 * nv) * dv * f.ev[i];
         }
-        F.depth = (float)dot(DS, f.n);
+        F.depth = g->parallel ? 0.f : (float)dot(DS, f.n);  // 0: no cosine weight (parallel FBP)
         F.u00 = (float)dot(P00S, f.eu);
         F.v00 = (float)dot(P00S, f.ev);
         F.beta = (float)(angles[3 * a] - angles[0]);
@@ -243,6 +286,13 @@ void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles,
     for (int a = 0; a < nAngles; ++a) {
         Frame f = frame(geo, angles, a);
         const double DSn = (f.D[0] - f.S[0]) * f.n[0] + (f.D[1] - f.S[1]) * f.n[1] + (f.D[2] - f.S[2]) * f.n[2];
+        if (geo->parallel) {  // no magnification; every ray has the central ray's obliquity
+            const double DS[3] = {f.D[0] - f.S[0], f.D[1] - f.S[1], f.D[2] - f.S[2]};
+            const double o = sqrt(dot(DS, DS)) / DSn;
+            if (o > obl) obl = o;
+            if (mag < 1.0) mag = 1.0;
+            continue;
+        }
         for (int q = 0; q < 4; ++q) {
             const double su = ((q & 1) ? 0.5 : -0.5) * geo->nDetector[0] * geo->dDetector[0];
             const double sv = ((q & 2) ? 0.5 : -0.5) * geo->nDetector[1] * geo->dDetector[1];
@@ -273,6 +323,7 @@ Grid make_grid(const tg_geometry *geo, int nAngles) {
     g.nu = geo->nDetector[0];
     g.nv = geo->nDetector[1];
     g.nA = nAngles;
+    g.parallel = geo->parallel ? 1 : 0;
     g.dx = (float)geo->dVoxel[0];
     g.dy = (float)geo->dVoxel[1];
     g.dz = (float)geo->dVoxel[2];

@@ -42,6 +42,20 @@ struct alignas(16) Angle {
     float D0hi[3], D0lo[3];
     float Uhi[3], Ulo[3];
     float Vhi[3], Vlo[3];
+    // Parallel beam (par = 1): S, Sg, Shi/Slo hold the start of pixel
+    // (0, 0)'s ray, dir0 / D0 the common direction D - S, and the start
+    // moves by U / d, V / d (index space, double-float) per pixel.  The FDK
+    // and brick-search constants then describe the parallel projection
+    // (n = 0, Sn = -1 so that L = 1; DSO = 1; tau = du).
+    float par;
+    float Uih[3], Uil[3];
+    float Vih[3], Vil[3];
+    // Parallel beam, Siddon: a point of pixel (0, 0)'s ray level with the
+    // volume centre (index space + 1/2, double-float) and its distance t0
+    // (mm) from the ray's start, so that the walk measures from a point of
+    // small magnitude.
+    float Cgh[3], Cgl[3];
+    float t0;
 };
 
 // Per-projection constants of the FDK pre-weights (mm, FP64-derived):
@@ -74,6 +88,7 @@ struct Grid {
     // one projection (matched backprojector fixed-point range).
     float wbound;
     float sdh[3], sdl[3];  // delta / d per axis, double-float
+    int parallel;          // parallel beam (tg_geometry.parallel)
 };
 
 // Epilogue modes of the forward projector.

@@ -62,16 +62,30 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
 
 // Ray (iu, iv) of angle A: step g and reference point p_kr (see above);
 // Ld = |P - S| / delta, the last admissible sample index (as a float).
+// PAR: parallel beam -- the direction is D - S for every ray and the start
+// S00 + iu U + iv V moves with the pixel instead (a template parameter, so
+// that the cone-beam kernels compile exactly as without it).
+template <bool PAR = false>
 __device__ __forceinline__ void ray_frame(const Angle &A, const Grid &g, int iu, int iv, Ray &r, float &Ld) {
     const float fu = (float)iu, fv = (float)iv;
-    float Dh[3], Dl[3];
+    float Dh[3], Dl[3], Oh[3], Ol[3];  // Oh, Ol: start of a parallel ray (index space)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float uh, ul, vh, vl, th, tl;
-        df_mulf(A.Uhi[i], A.Ulo[i], fu, uh, ul);
-        df_mulf(A.Vhi[i], A.Vlo[i], fv, vh, vl);
-        df_add(A.D0hi[i], A.D0lo[i], uh, ul, th, tl);
-        df_add(th, tl, vh, vl, Dh[i], Dl[i]);  // P - S (mm)
+        if constexpr (PAR) {
+            float uh, ul, vh, vl, th, tl;
+            df_mulf(A.Uih[i], A.Uil[i], fu, uh, ul);
+            df_mulf(A.Vih[i], A.Vil[i], fv, vh, vl);
+            df_add(A.Shi[i], A.Slo[i], uh, ul, th, tl);
+            df_add(th, tl, vh, vl, Oh[i], Ol[i]);
+            Dh[i] = A.D0hi[i];
+            Dl[i] = A.D0lo[i];
+        } else {
+            float uh, ul, vh, vl, th, tl;
+            df_mulf(A.Uhi[i], A.Ulo[i], fu, uh, ul);
+            df_mulf(A.Vhi[i], A.Vlo[i], fv, vh, vl);
+            df_add(A.D0hi[i], A.D0lo[i], uh, ul, th, tl);
+            df_add(th, tl, vh, vl, Dh[i], Dl[i]);  // P - S (mm)
+        }
     }
     float qh, ql;
     df_mul(Dh[0], Dl[0], Dh[0], Dl[0], qh, ql);
@@ -107,8 +121,16 @@ __device__ __forceinline__ void ray_frame(const Angle &A, const Grid &g, int iu,
     r.gz = __fadd_rn(Gh[2], Gl[2]);
     // reference: the sample closest to the volume centre (FP32; only needs
     // to be the same integer in every kernel)
-    const float cx = 0.5f * (float)(g.nx - 1) - A.Sg[0], cy = 0.5f * (float)(g.ny - 1) - A.Sg[1],
-                cz = 0.5f * (float)(g.nz - 1) - A.Sg[2];
+    float cx, cy, cz;
+    if constexpr (PAR) {
+        cx = 0.5f * (float)(g.nx - 1) - Oh[0];
+        cy = 0.5f * (float)(g.ny - 1) - Oh[1];
+        cz = 0.5f * (float)(g.nz - 1) - Oh[2];
+    } else {
+        cx = 0.5f * (float)(g.nx - 1) - A.Sg[0];
+        cy = 0.5f * (float)(g.ny - 1) - A.Sg[1];
+        cz = 0.5f * (float)(g.nz - 1) - A.Sg[2];
+    }
     const float num = fmaf(cz, r.gz, fmaf(cy, r.gy, __fmul_rn(cx, r.gx)));
     const float den = fmaf(r.gz, r.gz, fmaf(r.gy, r.gy, __fmul_rn(r.gx, r.gx)));
     const float kc = __fdiv_rn(num, den);
@@ -119,7 +141,10 @@ __device__ __forceinline__ void ray_frame(const Angle &A, const Grid &g, int iu,
     for (int i = 0; i < 3; ++i) {
         float mh, ml, sh2, sl2;
         df_mulf(Gh[i], Gl[i], kf, mh, ml);
-        df_add(A.Shi[i], A.Slo[i], mh, ml, sh2, sl2);
+        if constexpr (PAR)
+            df_add(Oh[i], Ol[i], mh, ml, sh2, sl2);
+        else
+            df_add(A.Shi[i], A.Slo[i], mh, ml, sh2, sl2);
         P[i] = __fadd_rn(sh2, sl2);
     }
     r.sx = P[0];
@@ -128,24 +153,33 @@ __device__ __forceinline__ void ray_frame(const Angle &A, const Grid &g, int iu,
     Ld = __fmul_rn(Lh, g.inv_delta);
 }
 
+
 // FP64 membership of sample k of pixel (iu, iv): the definition itself.
+template <bool PAR>
 static __device__ __noinline__ bool sample_inside_fp64(const Angle &A, const Grid &g, int iu, int iv, int k) {
     if (k < 0) return false;
     const double px = A.P00[0] + (double)iu * A.U[0] + (double)iv * A.V[0];
     const double py = A.P00[1] + (double)iu * A.U[1] + (double)iv * A.V[1];
     const double pz = A.P00[2] + (double)iu * A.U[2] + (double)iv * A.V[2];
-    const double dx = px - A.S[0], dy = py - A.S[1], dz = pz - A.S[2];
+    double ox = A.S[0], oy = A.S[1], oz = A.S[2];  // start of the ray
+    if constexpr (PAR) {
+        ox += (double)iu * A.U[0] + (double)iv * A.V[0];
+        oy += (double)iu * A.U[1] + (double)iv * A.V[1];
+        oz += (double)iu * A.U[2] + (double)iv * A.V[2];
+    }
+    const double dx = px - ox, dy = py - oy, dz = pz - oz;
     const double L = sqrt(dx * dx + dy * dy + dz * dz);
     const double t = (double)k * g.delta64;
     if (t > L) return false;
     // unit direction first, then S + t d: the order of the definition, so
     // that exact ties (a sample exactly on a face) resolve the same way
     const double ux = dx / L, uy = dy / L, uz = dz / L;
-    const double x = A.S[0] + t * ux, y = A.S[1] + t * uy, z = A.S[2] + t * uz;
+    const double x = ox + t * ux, y = oy + t * uy, z = oz + t * uz;
     return x >= -g.hx64 && x <= g.hx64 && y >= -g.hy64 && y <= g.hy64 && z >= -g.hz64 && z <= g.hz64;
 }
 
 // 1: inside, 0: outside; decided in FP32 unless within `margin` of a face.
+template <bool PAR>
 __device__ __forceinline__ bool sample_inside(const Angle &A, const Grid &g, const Ray &r, float L_over_delta,
                                               float margin, int iu, int iv, int k) {
     if (k < 0) return false;
@@ -158,13 +192,14 @@ __device__ __forceinline__ bool sample_inside(const Angle &A, const Grid &g, con
     const float tl = L_over_delta - (float)k;  // >= 0 when t_k <= L
     if (m > margin && tl > margin) return true;
     if (m < -margin || tl < -margin) return false;
-    return sample_inside_fp64(A, g, iu, iv, k);
+    return sample_inside_fp64<PAR>(A, g, iu, iv, k);
 }
 
 // Set up ray (iu, iv) of angle A.  Returns false when no sample is kept.
+template <bool PAR = false>
 __device__ __forceinline__ bool ray_setup(const Angle &A, const Grid &g, int iu, int iv, Ray &r) {
     float Ld;
-    ray_frame(A, g, iu, iv, r, Ld);
+    ray_frame<PAR>(A, g, iu, iv, r, Ld);
     float kmin = 0.f, kmax = Ld;
     const float sv[3] = {r.sx, r.sy, r.sz};
     const float gv[3] = {r.gx, r.gy, r.gz};
@@ -199,11 +234,11 @@ __device__ __forceinline__ bool ray_setup(const Angle &A, const Grid &g, int iu,
     // interval and the FP32 slab estimate is within a sample of its ends;
     // every loop is bounded (k >= 0, and no sample beyond |P - S| is inside).
     // Each walk is also capped at 8 steps (it takes one or two).
-    for (int s = 0; s < 8 && k0 > 0 && sample_inside(A, g, r, Ld, margin, iu, iv, k0 - 1); ++s) --k0;
-    for (int s = 0; s < 8 && k0 <= k1 && !sample_inside(A, g, r, Ld, margin, iu, iv, k0); ++s) ++k0;
+    for (int s = 0; s < 8 && k0 > 0 && sample_inside<PAR>(A, g, r, Ld, margin, iu, iv, k0 - 1); ++s) --k0;
+    for (int s = 0; s < 8 && k0 <= k1 && !sample_inside<PAR>(A, g, r, Ld, margin, iu, iv, k0); ++s) ++k0;
     if (k1 < k0 - 1) k1 = k0 - 1;
-    for (int s = 0; s < 8 && sample_inside(A, g, r, Ld, margin, iu, iv, k1 + 1); ++s) ++k1;
-    for (int s = 0; s < 8 && k1 >= k0 && !sample_inside(A, g, r, Ld, margin, iu, iv, k1); ++s) --k1;
+    for (int s = 0; s < 8 && sample_inside<PAR>(A, g, r, Ld, margin, iu, iv, k1 + 1); ++s) ++k1;
+    for (int s = 0; s < 8 && k1 >= k0 && !sample_inside<PAR>(A, g, r, Ld, margin, iu, iv, k1); ++s) --k1;
     r.k0 = k0;
     r.k1 = k1;
     return k0 <= k1;

@@ -56,6 +56,7 @@ class _CGeometry(ctypes.Structure):
         ("offDetector", ctypes.POINTER(ctypes.c_double)),
         ("rotDetector", ctypes.POINTER(ctypes.c_double)),
         ("COR", ctypes.POINTER(ctypes.c_double)),
+        ("parallel", ctypes.c_int32),
     ]
 
 
@@ -145,6 +146,7 @@ class _Geo:
         g.DSD0 = float(self.arrs[1][0]) if n else 1536.0
         for name, arr in zip(("DSO", "DSD", "offOrigin", "offDetector", "rotDetector", "COR"), self.arrs):
             setattr(g, name, arr.ctypes.data_as(_DP))
+        g.parallel = 1 if getattr(geo, "parallel", False) else 0
         self.g = g
         self.n = n
 

@@ -167,3 +167,16 @@ def test_parallel_fbp_reconstructs_ball(arc, centre, R):
     rr = np.sqrt((c[0][None, None, :] - m[0]) ** 2 + (c[1][None, :, None] - m[1]) ** 2 + 0 * c[2][:, None, None])
     inner = (rr < 0.6 * R) & (np.abs(c[2])[:, None, None] < 0.6 * R / 2)
     assert np.abs(x[inner] / mu - 1).max() < 0.02
+
+
+def test_parallel_frequency_filter_equals_spatial_filter():
+    """The windowed-filter path of the FDK variants reduces to the C
+    oracle's spatial ramp on parallel scans too (no pre-weight, pitch du)."""
+    from oracle import fdk_variants as ofdk
+    g = _par(n=3)
+    p = np.random.default_rng(6).standard_normal(g.proj_shape)
+    a = ofdk.fdk_filter(g, p, "ram-lak")
+    b = oracle.fdk_filter(g, p)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    with pytest.raises(ValueError):
+        ofdk.fdk_filter(g, p, parker=True)
