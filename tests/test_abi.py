@@ -179,3 +179,18 @@ def test_workspace_sizes_of_the_solvers(lib):
     g = _geo()
     for op in ("mlem", "osem", "asd_pocs", "lsqr", "lsmr"):
         assert tg.workspace_size(g, op, blocksize=2) > 4 * int(np.prod(g.vol_shape))
+
+
+def test_parallel_beam_refusals_on_the_host(lib):
+    """Parker / Wang weights are not defined for a parallel scan; the call
+    is refused before any CUDA call."""
+    import math
+    g = inputs.parallel_geometry((8, 8, 8), (1.0,) * 3, (10, 10), (1.5, 1.5), 6, arc=1.2 * math.pi,
+                                 DSO=100.0, DSD=160.0)
+    G = tg._Geo(g)
+    assert G.g.parallel == 1
+    p = np.zeros(g.proj_shape, np.float32)
+    v = np.zeros(g.vol_shape, np.float32)
+    assert lib.tg_fdk_ex(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 0, 1, None) == 6
+    assert lib.tg_fdk_filter(G.ref, G.ang, G.n, p.ctypes.data, v.ctypes.data, 0, 2, None) == 6
+    assert tg._Geo(_geo()).g.parallel == 0
