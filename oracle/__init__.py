@@ -281,16 +281,52 @@ def sirt(geo, b, niter: int, lam: float = 1.0, nonneg: bool = True, x0=None):
     return x, np.array(hist)
 
 
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state: int):
+    """One step of SplitMix64 (Steele, Lea and Flood 2014): returns (new
+    state, 64-bit output)."""
+    state = (state + 0x9E3779B97F4A7C15) & _MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return state, z ^ (z >> 31)
+
+
+def block_orders(n_blocks: int, niter: int, order: str = "sequential", seed: int = 0):
+    """The block order of every iteration: acquisition order, or (random)
+    a Fisher-Yates shuffle from the last position down, position k - 1
+    swapped with j = (next SplitMix64 output) mod k, one stream seeded once
+    for the whole run (Sec. 2.2.2 lists random orders; this is the reading)."""
+    state = int(seed) & _MASK64
+    out = []
+    for _ in range(niter):
+        perm = list(range(n_blocks))
+        if order == "random":
+            for k in range(n_blocks, 1, -1):
+                state, r = splitmix64(state)
+                j = r % k
+                perm[k - 1], perm[j] = perm[j], perm[k - 1]
+        elif order != "sequential":
+            raise ValueError(order)
+        out.append(perm)
+    return out
+
+
 def subsets(n_angles: int, blocksize: int):
     """Contiguous angle blocks of ``blocksize`` in acquisition order; the last
     block holds the remainder."""
     return [np.arange(s, min(s + blocksize, n_angles)) for s in range(0, n_angles, blocksize)]
 
 
-def ossart(geo, b, niter: int, blocksize: int, lam: float = 1.0, nonneg: bool = True, x0=None):
+def ossart(geo, b, niter: int, blocksize: int, lam: float = 1.0, nonneg: bool = True, x0=None,
+           order: str = "sequential", seed: int = 0):
     """OS-SART: for each block s in order, x <- P(x + lam V_s A_s^T W_s (b_s
     - A_s x)) (Sec. 2.2.2, Eq. 6 with the SART row/column weights).  One
-    iteration visits every block once.  Returns (x, residual history)."""
+    iteration visits every block once, in acquisition order or in the
+    seeded random order of ``block_orders``.  Returns (x, residual
+    history)."""
     nx, ny, nz = (int(v) for v in geo.nVoxel)
     b = _f64(b)
     x = np.zeros((nz, ny, nx)) if x0 is None else _f64(x0).copy()
@@ -298,8 +334,9 @@ def ossart(geo, b, niter: int, blocksize: int, lam: float = 1.0, nonneg: bool = 
     sub = [geo.subset(idx) for idx in blocks]
     weights = [sirt_weights(g) for g in sub]
     hist = []
-    for _ in range(niter):
-        for idx, g, (W, V) in zip(blocks, sub, weights):
+    for perm in block_orders(len(blocks), niter, order, seed):
+        for q in perm:
+            idx, g, (W, V) = blocks[q], sub[q], weights[q]
             r = W * (b[idx] - forward(g, x))
             x = x + lam * V * backproject(g, r, "matched")
             if nonneg:
@@ -354,7 +391,8 @@ def _safe_div(num: np.ndarray, den: np.ndarray) -> np.ndarray:
     return out
 
 
-def osem(geo, b, niter: int, blocksize: int, x0=None, method: str = "interp"):
+def osem(geo, b, niter: int, blocksize: int, x0=None, method: str = "interp", order: str = "sequential",
+         seed: int = 0):
     """OS-EM (Hudson and Larkin 1994): for each block s of consecutive angles
     in acquisition order,
         x <- x / (A_s^T 1) * A_s^T (b_s / (A_s x)),
@@ -372,8 +410,9 @@ def osem(geo, b, niter: int, blocksize: int, x0=None, method: str = "interp"):
     sub = [geo.subset(idx) for idx in blocks]
     sens = [backproject(g, np.ones(g.proj_shape), bp) for g in sub]
     hist = []
-    for _ in range(niter):
-        for idx, g, sv in zip(blocks, sub, sens):
+    for perm in block_orders(len(blocks), niter, order, seed):
+        for q in perm:
+            idx, g, sv = blocks[q], sub[q], sens[q]
             ratio = _safe_div(b[idx], forward(g, x, fp))
             x = np.where(sv != 0, x * _safe_inv(sv) * backproject(g, ratio, bp), x)
         hist.append(float(np.linalg.norm(forward(geo, x, fp) - b)))

@@ -125,3 +125,10 @@ def test_mlem_conserves_counts_on_gpu():
     s = oracle.backproject(g, np.ones(g.proj_shape), "matched")
     seen = oracle.forward(g, np.ones(g.vol_shape)) != 0
     assert np.sum(s * x1) == pytest.approx(np.sum(b[seen]), rel=1e-5)
+
+
+def test_osem_random_order_matches_oracle(em_problem):
+    g, b, _ = em_problem
+    x = tg.osem(g, dev(b), 2, blocksize=20, order="random", seed=11)
+    xr, _ = oracle.osem(g, b, 2, 20, order="random", seed=11)
+    assert rel_l2(host(x), xr) <= 1e-4, rel_l2(host(x), xr)

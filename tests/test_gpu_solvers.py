@@ -169,3 +169,12 @@ def test_lsmr_warm_start_and_zero_data(problem):
     assert rel_l2(host(x5), xr) <= RTOL
     z = tg.lsmr(g, dev(np.zeros(g.proj_shape)), 3, x0=torch.zeros(g.vol_shape, device="cuda"))
     assert torch.count_nonzero(z) == 0
+
+
+def test_ossart_random_order_matches_oracle(problem):
+    """The seeded random block order (SplitMix64 + Fisher-Yates, written
+    independently on both sides) gives the oracle's iterates."""
+    g, _, b = problem
+    x = tg.ossart(g, dev(b), 3, blocksize=7, order="random", seed=5)
+    xr, _ = oracle.ossart(g, b, 3, 7, order="random", seed=5)
+    assert rel_l2(host(x), xr) <= RTOL, rel_l2(host(x), xr)
