@@ -7,8 +7,12 @@
  *     b the projections, both in lexicographic order;
  *   - the scan geometry of Sec. 2.4 and the geometry-parameter table of
  *     Appendix B, every parameter except the sizes may vary per projection;
- *   - FDK (Sec. 2.1, direct methods), SIRT and OS-SART (Sec. 2.1, Kaczmarz
- *     type; Sec. 2.2.2, Eq. 6), CGLS (Sec. 2.1, Krylov methods).
+ *   - FDK (Sec. 2.1, direct methods) with several filters and Parker / Wang
+ *     weights, SIRT and OS-SART (Sec. 2.1, Kaczmarz type; Sec. 2.2.2,
+ *     Eq. 6), CGLS, LSQR and LSMR (Sec. 2.1, Krylov methods), MLEM / OS-EM
+ *     (Sec. 2.1, Eq. 5), ASD-POCS with TV or the adaptive-weighted TV of
+ *     Sec. 2.2's algorithm features;
+ *   - cone or parallel beams (tg_geometry.parallel).
  *
  * Layouts (all float32, C order, x fastest):
  *   volume       vol [batch][nz][ny][nx]
@@ -24,11 +28,13 @@
  * D + ((iu + 0.5) - nu/2) du eu + ((iv + 0.5) - nv/2) dv ev (the uv origin
  * is the bottom-left detector corner).
  *
- * Buffers: every float buffer may be device memory (asynchronous on
- * `stream`) or host memory (the call stages it through device memory,
- * copies the result back and returns after the stream has finished).  The
- * caller owns every buffer; the library never frees them.  Scratch memory
- * is taken with cudaMallocAsync on `stream` and released before return.
+ * Buffers: every float buffer of the projector and solver calls may be
+ * device memory (asynchronous on `stream`) or host memory (the call stages
+ * it through device memory, copies the result back and returns after the
+ * stream has finished); the batched, TV and network calls take device
+ * memory only.  The caller owns every buffer; the library never frees
+ * them.  Scratch memory is taken with cudaMallocAsync on `stream` and
+ * released before return (tg_workspace_size reports how much).
  *
  * Errors: argument and geometry checks run on the host before any launch
  * and return synchronously; kernel launch errors are read with
