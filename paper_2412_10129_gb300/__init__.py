@@ -1,9 +1,13 @@
-"""GB300-native cone-beam CT projectors and iterative reconstruction.
+"""GB300-native cone- and parallel-beam CT projectors, iterative and learned
+reconstruction.
 
 The compute path is the CUDA library ``libtg`` (``csrc/``, C ABI declared in
 ``include/tg.h``); ``tg`` is its thin Python binding (argument marshalling
 only; the library is loaded on first use).  ``inputs`` draws seeded
-synthetic scans and phantoms.
+synthetic scans and phantoms; ``autograd`` wraps the projector pair as
+``torch.autograd.Function``s; ``learned`` is the learned-gradient scheme;
+``build`` compiles the library in-tree; ``profile_cases`` holds the small
+workloads of the profiler captures.
 """
 from . import inputs, tg  # noqa: F401
 
