@@ -1,0 +1,44 @@
+/*
+ * tg_probe.h -- gather-rate microbenchmarks (library libtgprobe.so).
+ *
+ * Measurement support, not part of the reconstruction path: the ceilings
+ * against which the interpolated projector and its transpose are reported.
+ * Their unit of work is a trilinear sample, eight voxels read from a 2x2x2
+ * neighbourhood (32 bytes of FP32 data, two 2x2 texture gathers); the paper
+ * (TIGRE v3, Sec. 2.5 on GPU acceleration) names no such rate, so these
+ * calls measure it on the device at hand.
+ *
+ * Every call runs on the current CUDA device, allocates and frees its own
+ * buffers (cudaMalloc / cudaMalloc3DArray), times `reps` launches with CUDA
+ * events on a private stream after one untimed launch, and returns 0 or the
+ * cudaError_t value that stopped it (invalid sizes: cudaErrorInvalidValue).
+ */
+#ifndef TG_PROBE_H
+#define TG_PROBE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Random 32-byte sectors over a working set of the largest power-of-two
+ * sector count not above `bytes` (at least 1024 sectors, at most 2^31),
+ * loaded through L2 only.  *gbs: sector bytes per second / 1e9;
+ * *ms_per_launch (nullable): average launch time. */
+int tgp_sector_gather(size_t bytes, int reps, double *gbs, double *ms_per_launch);
+
+/* 2x2 FP32 texture gathers (tld4) in pairs of neighbouring layers of an
+ * nx x ny x nlayers layered array (16 <= nx, ny <= 32768, 2 <= nlayers <=
+ * 2048; contents left uninitialised).  coherent != 0: the 32 lanes of a warp
+ * sit on an 8 x 4 patch of positions half a texel apart around a random
+ * point, else each lane draws its own random position.
+ * *gathers_per_s: lane gathers per second. */
+int tgp_tex_gather(int nx, int ny, int nlayers, int coherent, int reps, double *gathers_per_s,
+                   double *ms_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TG_PROBE_H */

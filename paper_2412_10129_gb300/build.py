@@ -1,7 +1,9 @@
 """Build libtg (the CUDA library behind include/tg.h) in-tree for sm_103a.
 
 Each ``csrc/*.cu`` file is compiled by nvcc in parallel, then linked into
-``lib/libtg.so``.  Nothing is installed outside the source tree.
+``lib/libtg.so``.  ``csrc/probe/tg_probe.cu`` (the gather-rate
+microbenchmarks of include/tg_probe.h, measurement support only) becomes
+``lib/libtgprobe.so``.  Nothing is installed outside the source tree.
 """
 from __future__ import annotations
 
@@ -16,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(LIB_DIR, "obj")
 LIB_PATH = os.path.join(LIB_DIR, "libtg.so")
+PROBE_SRC = os.path.join(CSRC, "probe", "tg_probe.cu")
+PROBE_PATH = os.path.join(LIB_DIR, "libtgprobe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -54,15 +58,28 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
+def _build_probe(force: bool) -> None:
+    hdr = os.path.join(HERE, "..", "include", "tg_probe.h")
+    if force or _stale(PROBE_PATH, [PROBE_SRC, hdr]):
+        tmp = PROBE_PATH + f".tmp{os.getpid()}"
+        cmd = [nvcc()] + NVCC_FLAGS + ["-shared", PROBE_SRC, "-o", tmp, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PROBE_PATH)
+
+
 def build(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
-    """Compile and link libtg; returns the path of the shared library."""
+    """Compile and link libtg (and libtgprobe); returns the path of libtg."""
     os.makedirs(OBJ_DIR, exist_ok=True)
     srcs = _sources()
     if force:
         for o in glob.glob(os.path.join(OBJ_DIR, "*.o")):
             os.remove(o)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs) + 1)) as ex:
+        probe = ex.submit(_build_probe, force)
         objs = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
+        probe.result()
     if force or _stale(LIB_PATH, objs):
         tmp = LIB_PATH + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]

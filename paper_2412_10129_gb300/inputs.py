@@ -282,6 +282,14 @@ def porous_cylinder(geo: Geometry, seed: int, n_pores: int = 500, mu: float = 0.
     return vol
 
 
+def micro_phantom(geo: Geometry, seed: int, n_ellipsoids: int = 200) -> np.ndarray:
+    """Phantom of the micro-CT workload: n seeded ellipsoids (the recipe
+    above) added to a porous cylinder drawn from the next seed."""
+    vol = ellipsoid_phantom(geo, n_ellipsoids, seed)
+    vol += porous_cylinder(geo, seed + 1)
+    return vol
+
+
 def random_volume(geo: Geometry, seed: int, dtype=np.float32) -> np.ndarray:
     """Uniform [0, 1) voxel values (white-noise volume for operator checks)."""
     return np.random.default_rng(seed).random(geo.vol_shape).astype(dtype)

@@ -37,6 +37,19 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_probe_library_exports_its_header():
+    """libtgprobe (the gather-rate microbenchmarks of include/tg_probe.h)
+    builds and exports what its header declares."""
+    from paper_2412_10129_gb300 import probe
+    build.build()
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "tg_probe.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(tgp_[a-z0-9_]+)\s*\(", text)))
+    assert names == ["tgp_sector_gather", "tgp_tex_gather"]
+    lib = probe.load()
+    for name in names:
+        assert hasattr(lib, name), name
+
+
 def test_status_strings(lib):
     assert tg.status_string(0) == "ok"
     assert tg.status_string(2) == "invalid geometry"
