@@ -1,15 +1,16 @@
 // tg_noalloc.cu -- tg_backproject_noalloc: the backprojectors for callers
 // that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the time they backproject: code
-// running while a CUDA graph is being built around it, code inside a host
-// that owns a fixed memory budget and forbids allocation after start-up, or
-// real-time paths that cannot afford an allocator's latency or its failure.
-// This entry point takes the same arguments as tg_backproject for device
-// buffers only and allocates nothing: its scratch (the per-angle constants
-// and, for TG_MATCHED, one max-|y| word per batch item) lives in the
-// file-scope device array below, which every GPU that loads the library holds
-// until the process exits.
+// Some callers cannot call cudaMalloc at the time they backproject: a host
+// process that reserves its whole device-memory budget at start-up and
+// forbids allocation afterwards (another allocator owns the rest of the
+// GPU), or a real-time path that cannot afford an allocator's latency or the
+// chance of its failure in the middle of a reconstruction.  This entry point
+// takes the same arguments as tg_backproject for device buffers only and
+// allocates nothing: its scratch (the per-angle constants and, for
+// TG_MATCHED, one max-|y| word per batch item) lives in the file-scope device
+// array below, which every GPU that loads the library holds until the
+// process exits.
 #include <math.h>
 
 #include <mutex>
@@ -24,7 +25,22 @@ constexpr int NOALLOC_MAX_BATCH = 256;
 constexpr size_t NOALLOC_ANGLE_BYTES = sizeof(Angle) * NOALLOC_MAX_ANGLES;
 constexpr size_t NOALLOC_BYTES = NOALLOC_ANGLE_BYTES + sizeof(unsigned int) * NOALLOC_MAX_BATCH;
 constexpr int NOALLOC_MAX_DEVICES = 64;
-constexpr int NOALLOC_CHUNK = 64;  // angles built on the host stack per copy
+constexpr int NOALLOC_CHUNK = 64;  // angles built on the host stack per launch
+
+// A chunk of per-angle constants, passed by value as a kernel parameter
+// (64 x 400 B, within the 32 KB parameter limit of sm_70 and later): the
+// launch copies it, so no host buffer has to outlive the call.
+struct AngleChunk {
+    Angle a[NOALLOC_CHUNK];
+};
+static_assert(sizeof(AngleChunk) <= 32000, "kernel parameter size");
+
+__global__ void k_store_angles(const __grid_constant__ AngleChunk c, Angle *dst, int n) {
+    const int words = (int)(sizeof(Angle) / sizeof(float4));
+    const float4 *src = reinterpret_cast<const float4 *>(c.a);
+    float4 *out = reinterpret_cast<float4 *>(dst);
+    for (int i = threadIdx.x; i < n * words; i += blockDim.x) out[i] = src[i];
+}
 
 // The scratch itself.  In host code its name is only a stand-in for the
 // symbol, never a device address: the address is looked up per device.
@@ -51,13 +67,17 @@ cudaError_t noalloc_scratch(void **out) {
     return cudaSuccess;
 }
 
+// Device memory of the current device, or managed memory.
 bool is_device_buffer(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -87,10 +107,11 @@ extern "C" tg_status tg_backproject_noalloc(const tg_geometry *geo, const double
     if (e != cudaSuccess) return TG_ERR_CUDA;
     Angle *dA = reinterpret_cast<Angle *>(base);
     unsigned int *amax = reinterpret_cast<unsigned int *>(static_cast<unsigned char *>(base) + NOALLOC_ANGLE_BYTES);
-    // Per-angle constants in chunks built on the stack: no host heap either.
-    // A copy from pageable memory returns once the source has been staged,
-    // so the chunk buffer can be refilled at once.
-    Angle chunk[NOALLOC_CHUNK];
+    // Per-angle constants in chunks built on the host stack (no host heap
+    // either) and stored into the scratch by a kernel that receives the
+    // chunk as its parameter.
+    static_assert(sizeof(Angle) % sizeof(float4) == 0, "Angle is copied as float4 words");
+    AngleChunk chunk;
     for (int a0 = 0; a0 < nAngles; a0 += NOALLOC_CHUNK) {
         const int n = nAngles - a0 < NOALLOC_CHUNK ? nAngles - a0 : NOALLOC_CHUNK;
         tg_geometry sub = *geo;
@@ -100,8 +121,10 @@ extern "C" tg_status tg_backproject_noalloc(const tg_geometry *geo, const double
         if (sub.offDetector) sub.offDetector += 2 * a0;
         if (sub.rotDetector) sub.rotDetector += 3 * a0;
         if (sub.COR) sub.COR += a0;
-        build_angles(&sub, angles + 3 * a0, n, chunk);
-        e = cudaMemcpyAsync(dA + a0, chunk, sizeof(Angle) * n, cudaMemcpyHostToDevice, s);
+        build_angles(&sub, angles + 3 * a0, n, chunk.a);
+        k_store_angles<<<1, 128, 0, s>>>(chunk, dA + a0, n);
+        count_launch();
+        e = cudaGetLastError();
         if (e != cudaSuccess) return TG_ERR_CUDA;
     }
     Grid g = make_grid(geo, nAngles);

@@ -1,10 +1,13 @@
 """tg_backproject_noalloc: the backprojection entry point for callers that
-cannot allocate device memory (code being captured into a CUDA graph, hosts
-with a fixed device-memory budget, latency-bound paths).  It must give the
-results of tg_backproject through the C ABI, call after call, while using
-only its static scratch.  This file runs last so that a stop at the first
-failure has already run every other test."""
+cannot allocate device memory (a host that fixes its device-memory budget at
+start-up, real-time paths that cannot afford an allocator's latency or
+failure).  It must give the results of tg_backproject through the C ABI,
+call after call, while using only its static scratch, and must take no
+memory from the device allocator.  This file runs last so that a stop at the
+first failure has already run every other test."""
 import ctypes
+import ctypes.util
+import os
 
 import numpy as np
 import pytest
@@ -31,13 +34,13 @@ def _geo():
 
 def _raw(lib, g, proj, vol, method, batch):
     G = tg._Geo(g)
-    code = {"matched": tg.TG_MATCHED, "fdk": tg.TG_FDK_WEIGHT}[method]
+    code = {"matched": tg.TG_MATCHED, "fdk": tg.TG_FDK_WEIGHT, "siddon": tg.TG_SIDDON_BP}[method]
     return lib.tg_backproject_noalloc(G.ref, G.ang, G.n, ctypes.c_void_p(proj.data_ptr()),
                                       ctypes.c_void_p(vol.data_ptr()), code, batch,
                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("method", ["matched", "fdk"])
+@pytest.mark.parametrize("method", ["matched", "fdk", "siddon"])
 def test_noalloc_matches_backproject_on_consecutive_calls(lib, method):
     g = _geo()
     for seed in (1, 2):   # two calls in a row: the shared scratch is refilled
@@ -80,3 +83,56 @@ def test_noalloc_rejects_what_it_cannot_serve(lib):
     assert _raw(lib, g, y, out, "matched", 1) == 0
     torch.cuda.synchronize()
     assert rel_l2(out.cpu().numpy(), tg.backproject(g, y, "matched").cpu().numpy()) <= TOL_L2
+
+
+def _cudart():
+    for name in (ctypes.util.find_library("cudart"), "/usr/local/cuda/lib64/libcudart.so", "libcudart.so"):
+        if name:
+            try:
+                return ctypes.CDLL(name)
+            except OSError:
+                continue
+    pytest.skip("libcudart not found")
+
+
+USED_MEM_HIGH = 8   # cudaMemPoolAttrUsedMemHigh
+
+
+def _pool_high(rt, pool):
+    v = ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, USED_MEM_HIGH, ctypes.byref(v)) == 0
+    return v.value
+
+
+def _pool_reset(rt, pool):
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+
+def test_noalloc_takes_no_device_memory(lib):
+    """The device's default memory pool (where cudaMallocAsync draws from)
+    keeps its high-water mark and the free device memory stays the same
+    across warmed-up calls of every method; tg_backproject, which takes its
+    scratch from that pool, raises the mark (the check can see an
+    allocation)."""
+    rt = _cudart()
+    dev = torch.cuda.current_device()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    g = _geo()
+    y = torch.from_numpy(inputs.random_projections(g, seed=7)).cuda()
+    out = torch.empty(g.vol_shape, device="cuda")
+    for method in ("matched", "fdk", "siddon"):
+        assert _raw(lib, g, y, out, method, 1) == 0   # warm-up (first-call set-up)
+    torch.cuda.synchronize()
+    _pool_reset(rt, pool)
+    base = _pool_high(rt, pool)
+    free0 = torch.cuda.mem_get_info()[0]
+    for method in ("matched", "fdk", "siddon"):
+        assert _raw(lib, g, y, out, method, 1) == 0
+        torch.cuda.synchronize()
+        assert _pool_high(rt, pool) == base, method
+    assert torch.cuda.mem_get_info()[0] == free0
+    tg.backproject(g, y, "matched", out=out)
+    torch.cuda.synchronize()
+    assert _pool_high(rt, pool) > base
