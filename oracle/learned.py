@@ -54,17 +54,16 @@ def step(geo, x, b, Ws, Bs, sx, sg, so, round_act=None):
 
 
 def step_backward(geo, x, b, Ws, Bs, sx, sg, so, gbar, round_act=None):
-    """Gradients of L = <gbar, x'> in x, in every W and in every bias.
-    ``round_act`` (e.g. conv.bf16_round) mirrors a reduced-precision
-    implementation: the forward activations are rounded as in ``step`` and
-    so is every layer's incoming gradient (the network's output gradient
-    and the gradient in each layer's input)."""
+    """Gradients of L = <gbar, x'> in x, in every W and in every bias, in
+    FP64.  ``round_act`` (e.g. conv.bf16_round) rounds the network input and
+    the hidden activations of the forward pass as in ``step`` -- the
+    precision the learned network's definition fixes for its activations --
+    so the gradient is the exact chain rule of that network; the gradients
+    themselves are never rounded."""
     _, acts = step(geo, x, b, Ws, Bs, sx, sg, so, round_act=round_act)
-    rnd = (lambda a: a) if round_act is None else (lambda a: np.asarray(round_act(a), np.float64))
     gbar = np.asarray(gbar, np.float64)
     gy = np.zeros(acts[-1].shape[:4] + (Ws[-1].shape[4],))
     gy[0, ..., 0] = so * gbar
-    gy = rnd(gy)
     dWs, dBs = [None] * len(Ws), [None] * len(Ws)
     for li in range(len(Ws) - 1, -1, -1):
         dWs[li] = conv.conv3d_backward_weight(acts[li], gy)
@@ -72,6 +71,6 @@ def step_backward(geo, x, b, Ws, Bs, sx, sg, so, gbar, round_act=None):
         g_in = conv.conv3d_backward_data(gy, Ws[li])
         if li > 0:
             g_in = g_in * (acts[li] > 0)
-        gy = rnd(g_in)
+        gy = g_in
     gx = gbar + sx * gy[0, ..., 0] + _data_gradient(geo, sg * gy[0, ..., 1], None)
     return gx, dWs, dBs

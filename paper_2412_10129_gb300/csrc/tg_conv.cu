@@ -59,7 +59,8 @@ struct ConvTable {
 
 // Persistent CTAs: the weights are staged once per CTA, then the CTA walks
 // work items with a grid stride; each warp computes 32 voxels x COUT.
-template <int CIN, int COUT, bool RELU, bool OUT_F32>
+// OUT: 0 = BF16 store, 1 = FP32 store, 2 = FP32 added to y.
+template <int CIN, int COUT, bool RELU, int OUT>
 __global__ void __launch_bounds__(128) k_conv3d(const bf16 *__restrict__ x, const float *__restrict__ wt,
                                                 const float *__restrict__ bias, void *__restrict__ y,
                                                 const ConvTable tab) {
@@ -156,7 +157,11 @@ __global__ void __launch_bounds__(128) k_conv3d(const bf16 *__restrict__ x, cons
                         v1 = fmaxf(v1, 0.f);
                     }
                     const size_t e = (orow + xo) * COUT + o;
-                    if (OUT_F32) {
+                    if (OUT == 2) {
+                        float2 *d2 = reinterpret_cast<float2 *>(reinterpret_cast<float *>(y) + e);
+                        const float2 o2 = *d2;
+                        *d2 = make_float2(o2.x + v0, o2.y + v1);
+                    } else if (OUT == 1) {
                         *reinterpret_cast<float2 *>(reinterpret_cast<float *>(y) + e) = make_float2(v0, v1);
                     } else {
                         *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(y) + e) =
@@ -394,6 +399,50 @@ __global__ void k_lg_unpack(const bf16 *__restrict__ in, int C, float *__restric
     }
 }
 
+// Gradient as a pair of BF16 tensors: hi = bf16(m g), lo = bf16(m g - hi),
+// m = (act > 0) when act is given (the ReLU mask of the layer's input),
+// else 1.  hi + lo carries g to about 2^-17 of its magnitude, so that the
+// BF16 tensor-core kernels applied to both halves (and summed in FP32) see
+// the FP32 gradient instead of its BF16 rounding.
+__global__ void k_grad_split(const float *__restrict__ g, const bf16 *__restrict__ act, bf16 *__restrict__ hi,
+                             bf16 *__restrict__ lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = (act == nullptr || __bfloat162float(act[i]) > 0.f) ? g[i] : 0.f;
+        const bf16 h = __float2bfloat16(v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16(v - __bfloat162float(h));
+    }
+}
+
+// a [nvox] FP32 -> the pair (hi, lo) of [nvox][C] BF16 = (sa a, 0, ..., 0), C in {8, 16}
+__global__ void k_lg_pack_split(const float *__restrict__ a, bf16 *__restrict__ hi, bf16 *__restrict__ lo,
+                                size_t nvox, int C, float sa) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+        const float x = sa * a[v];
+        const bf16 h = __float2bfloat16(x);
+        const bf16 l = __float2bfloat16(x - __bfloat162float(h));
+        const unsigned hu = (unsigned)__bfloat16_as_ushort(h), lu = (unsigned)__bfloat16_as_ushort(l);
+        uint4 *ph = reinterpret_cast<uint4 *>(hi + v * C);
+        uint4 *pl = reinterpret_cast<uint4 *>(lo + v * C);
+        ph[0] = make_uint4(hu, 0u, 0u, 0u);
+        pl[0] = make_uint4(lu, 0u, 0u, 0u);
+        if (C == 16) {
+            ph[1] = make_uint4(0u, 0u, 0u, 0u);
+            pl[1] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// [nvox][C] FP32 -> a (=|+=) sa channel 0, b = sb channel 1 (b may be null)
+__global__ void k_lg_unpack_f32(const float *__restrict__ in, int C, float *__restrict__ a, float *__restrict__ b,
+                                size_t nvox, float sa, float sb, int accumulate) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+        const float c0 = sa * in[v * C];
+        a[v] = accumulate ? a[v] + c0 : c0;
+        if (b) b[v] = sb * in[v * C + 1];
+    }
+}
+
 // x_next[v] = x[v] + so net[v][0] (the network's last layer has padded channels)
 __global__ void k_lg_update(const float *x, const float *__restrict__ net, float *xn, size_t nvox, int stride,
                             float so) {
@@ -409,11 +458,11 @@ int sm_count() {
     return n > 0 ? n : 152;
 }
 
-template <int CIN, int COUT, bool RELU, bool OUT_F32>
+template <int CIN, int COUT, bool RELU, int OUT>
 cudaError_t run_conv(const bf16 *x, const float *w, const float *bias, void *y, const ConvTable &tab,
                      cudaStream_t s) {
     const int smem = 27 * COUT * CIN * 2;
-    auto kern = k_conv3d<CIN, COUT, RELU, OUT_F32>;
+    auto kern = k_conv3d<CIN, COUT, RELU, OUT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -433,10 +482,11 @@ cudaError_t dispatch_conv(const void *x, const float *w, const float *bias, void
     const bf16 *xb = (const bf16 *)x;
 #define TG_CONV_CASE(CI, CO)                                                                                   \
     if (cin == CI && cout == CO) {                                                                             \
-        if (relu && out_f32) return run_conv<CI, CO, true, true>(xb, w, bias, y, tab, s);                      \
-        if (relu) return run_conv<CI, CO, true, false>(xb, w, bias, y, tab, s);                                \
-        if (out_f32) return run_conv<CI, CO, false, true>(xb, w, bias, y, tab, s);                             \
-        return run_conv<CI, CO, false, false>(xb, w, bias, y, tab, s);                                         \
+        if (out_f32 == 2) return relu ? cudaErrorInvalidValue : run_conv<CI, CO, false, 2>(xb, w, bias, y, tab, s); \
+        if (relu && out_f32) return run_conv<CI, CO, true, 1>(xb, w, bias, y, tab, s);                         \
+        if (relu) return run_conv<CI, CO, true, 0>(xb, w, bias, y, tab, s);                                    \
+        if (out_f32) return run_conv<CI, CO, false, 1>(xb, w, bias, y, tab, s);                                \
+        return run_conv<CI, CO, false, 0>(xb, w, bias, y, tab, s);                                             \
     }
     TG_CONV_CASE(16, 32)
     TG_CONV_CASE(32, 32)
@@ -528,9 +578,11 @@ cudaError_t run_wgrad_mma(const void *x, const void *gy, float *dw, int N, int Z
 }
 
 cudaError_t launch_conv3d_wgrad(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, int cin,
-                                int cout, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * 27 * cin * cout, s);
-    if (e != cudaSuccess) return e;
+                                int cout, cudaStream_t s, int zero) {
+    if (zero) {
+        cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * 27 * cin * cout, s);
+        if (e != cudaSuccess) return e;
+    }
     if (cin == 16 && cout == 32) return run_wgrad_mma<16, 32>(x, gy, dw, N, Z, Y, X, s);
     if (cin == 32 && cout == 32) return run_wgrad_mma<32, 32>(x, gy, dw, N, Z, Y, X, s);
     if (cin == 32 && cout == 8) return run_wgrad_mma<32, 8>(x, gy, dw, N, Z, Y, X, s);
@@ -566,8 +618,8 @@ cudaError_t launch_flip_weights(const float *w, float *wb, int cin, int cout, cu
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_bias_grad(const void *gy, float *db, size_t nvox, int cout, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(db, 0, sizeof(float) * cout, s);
+cudaError_t launch_bias_grad(const void *gy, float *db, size_t nvox, int cout, cudaStream_t s, int zero) {
+    cudaError_t e = zero ? cudaMemsetAsync(db, 0, sizeof(float) * cout, s) : cudaSuccess;
     if (e != cudaSuccess || nvox == 0) return e;
     size_t nb = (nvox + 31) / 32;
     if (nb > 152 * 8) nb = 152 * 8;
@@ -605,6 +657,35 @@ cudaError_t launch_lg_unpack(const void *in, int C, float *a, float *b, size_t n
     size_t nb = (nvox + 255) / 256;
     if (nb > 152 * 16) nb = 152 * 16;
     k_lg_unpack<<<(unsigned)nb, 256, 0, s>>>((const bf16 *)in, C, a, b, nvox, sa, sb, accumulate);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_split(const float *g, const void *act, void *hi, void *lo, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    size_t nb = (n + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_grad_split<<<(unsigned)nb, 256, 0, s>>>(g, (const bf16 *)act, (bf16 *)hi, (bf16 *)lo, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lg_pack_split(const float *a, void *hi, void *lo, size_t nvox, int C, float sa, cudaStream_t s) {
+    if (nvox == 0) return cudaSuccess;
+    if (C != 8 && C != 16) return cudaErrorInvalidValue;
+    size_t nb = (nvox + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_lg_pack_split<<<(unsigned)nb, 256, 0, s>>>(a, (bf16 *)hi, (bf16 *)lo, nvox, C, sa);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lg_unpack_f32(const float *in, int C, float *a, float *b, size_t nvox, float sa, float sb,
+                                 int accumulate, cudaStream_t s) {
+    if (nvox == 0) return cudaSuccess;
+    size_t nb = (nvox + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_lg_unpack_f32<<<(unsigned)nb, 256, 0, s>>>(in, C, a, b, nvox, sa, sb, accumulate);
     count_launch();
     return cudaGetLastError();
 }

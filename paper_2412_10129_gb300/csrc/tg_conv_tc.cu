@@ -65,6 +65,12 @@ struct TcParams {
 static_assert(sizeof(TcParams) <= 4096, "kernel parameter size");
 
 __device__ int g_tc_error;
+// Test hooks (tg_test_conv_wait): the budget of a role's wait, and a switch
+// that makes the epilogue wait on a barrier that nothing arrives at, so that
+// its wait runs out and the whole CTA takes the error path.  Teardown waits
+// (mbar_drain) always keep the full TC_WAIT_CYCLES.
+__device__ long long g_tc_wait_cycles = TC_WAIT_CYCLES;
+__device__ int g_tc_stall;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -90,14 +96,14 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
     return ok != 0;
 }
 // Waits for the phase of `parity` to complete.  False when the CTA's error
-// flag is (or becomes, after TC_WAIT_CYCLES) set.
-__device__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *err) {
+// flag is (or becomes, after `budget` cycles) set.
+__device__ bool mbar_wait(unsigned bar, unsigned parity, volatile int *err, long long budget) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*err) return false;
-        if (clock64() - t0 > TC_WAIT_CYCLES) {
+        if (clock64() - t0 > budget) {
             *err = 1;
             return false;
         }
@@ -214,7 +220,7 @@ struct TcShape {
     static constexpr int WPAIR = NP * CIN * 2;              // weight bytes per (dz, dy)
     static_assert(WPAIR % (8 * ROWB) == 0, "weight blocks keep the swizzle phase");
     static constexpr int TCOLS = 2 * NP <= 32 ? 32 : 2 * NP <= 64 ? 64 : 2 * NP <= 128 ? 128 : 256;
-    static constexpr int NBAR = 2 * TC_STAGES + 7;          // full, empty, tfull x2, tempty x2, done, mdone x2
+    static constexpr int NBAR = 2 * TC_STAGES + 8;          // full, empty, tfull x2, tempty x2, done, mdone x2, stall
     // + a guard band, so that descriptor strides read under either reading
     // of their leading/stride fields stay inside the allocation
     static constexpr int GUARD = 2048;
@@ -224,7 +230,8 @@ struct TcShape {
         (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NP >> 3) << 17) | ((unsigned)(TC_M >> 4) << 24);
 };
 
-template <int CIN, int COUT, bool RELU, bool OUT_F32>
+// OUT: 0 = BF16 store, 1 = FP32 store, 2 = FP32 added to y.
+template <int CIN, int COUT, bool RELU, int OUT>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__restrict__ wt,
                                                           const float *__restrict__ bias, void *__restrict__ y,
                                                           const __grid_constant__ TcParams p) {
@@ -246,6 +253,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
     auto tempty = [&](int b) { return bar0 + 8u * (2 * TC_STAGES + 2 + b); };
     const unsigned done = bar0 + 8u * (2 * TC_STAGES + 4);
     auto mdone = [&](int b) { return bar0 + 8u * (2 * TC_STAGES + 5 + b); };
+    const unsigned stallbar = bar0 + 8u * (2 * TC_STAGES + 7);  // never arrived at (test hook)
+    const long long budget = g_tc_wait_cycles;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int *err = &s_err;
 
@@ -261,6 +270,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
             mbar_init(mdone(b), 1);
         }
         mbar_init(done, 1);
+        mbar_init(stallbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // weights -> BF16 B operands, one per (dz, dy): row n = tap * CO + o of
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
                 bool ok = true;
                 for (int k = 0; k < 9; ++k, ++q) {
                     const int s = q % TC_STAGES;
-                    if (!mbar_wait(empty(s), ((q / TC_STAGES) & 1) ^ 1, err)) {
+                    if (!mbar_wait(empty(s), ((q / TC_STAGES) & 1) ^ 1, err, budget)) {
                         ok = false;
                         break;
                     }
@@ -330,7 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
             int uses[2] = {0, 0};  // completed mdone phases per buffer
             bool ok = true;
             auto finish = [&](int b) -> bool {
-                if (!mbar_wait(mdone(b), uses[b] & 1, err)) return false;
+                if (!mbar_wait(mdone(b), uses[b] & 1, err, budget)) return false;
                 ++uses[b];
                 tc_fence_after();
                 const unsigned db = tmem + (unsigned)(b * S::NP);
@@ -345,12 +355,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
             };
             for (int it = blockIdx.x; it < total && ok; it += gridDim.x, ++t) {
                 const int buf = t & 1;
-                if (!mbar_wait(tempty(buf), ((t >> 1) & 1) ^ 1, err)) break;
+                if (!mbar_wait(tempty(buf), ((t >> 1) & 1) ^ 1, err, budget)) break;
                 tc_fence_after();
                 const unsigned d = tmem + (unsigned)(buf * S::NP);
                 for (int k = 0; k < 9; ++k, ++q) {
                     const int s = q % TC_STAGES;
-                    if (!mbar_wait(full(s), (q / TC_STAGES) & 1, err)) {
+                    if (!mbar_wait(full(s), (q / TC_STAGES) & 1, err, budget)) {
                         ok = false;
                         break;
                     }
@@ -386,10 +396,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
 #pragma unroll
         for (int o = 0; o < CO; ++o) bv[o] = (bias && o < COUT) ? bias[o] : 0.f;
         int t = 0;
-        for (int it = blockIdx.x; it < total; it += gridDim.x, ++t) {
+        if (g_tc_stall) {  // test hook: a wait that runs out
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait(stallbar, 0, err, budget) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) t = -1;
+        }
+        for (int it = blockIdx.x; it < total && t >= 0; it += gridDim.x, ++t) {
             const int buf = t & 1;
             int ok = 0;
-            if (lane == 0) ok = mbar_wait(tfull(buf), (t >> 1) & 1, err) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(tfull(buf), (t >> 1) & 1, err, budget) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
@@ -419,7 +435,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
             const int xo = w.x0 + lane;
             if (w.valid && lane < TC_Q && xo < p.X[w.v]) {
                 const size_t vox = (size_t)p.vox0[w.v] + ((size_t)w.z * p.Y[w.v] + w.y) * p.X[w.v] + xo;
-                if (OUT_F32) {
+                if (OUT == 2) {
+                    float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + vox * COUT);
+#pragma unroll
+                    for (int c = 0; c < COUT / 4; ++c) {
+                        const float4 o4 = dst[c];
+                        dst[c] = make_float4(o4.x + out[4 * c], o4.y + out[4 * c + 1], o4.z + out[4 * c + 2],
+                                             o4.w + out[4 * c + 3]);
+                    }
+                } else if (OUT == 1) {
                     float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + vox * COUT);
 #pragma unroll
                     for (int c = 0; c < COUT / 4; ++c)
@@ -490,10 +514,10 @@ int sm_count_tc() {
     return n > 0 ? n : 152;
 }
 
-template <int CIN, int COUT, bool RELU, bool OUT_F32>
+template <int CIN, int COUT, bool RELU, int OUT>
 cudaError_t run_tc(const float *w, const float *bias, void *y, const TcParams &p, cudaStream_t s) {
     using S = TcShape<CIN, COUT>;
-    auto kern = k_conv3d_tc<CIN, COUT, RELU, OUT_F32>;
+    auto kern = k_conv3d_tc<CIN, COUT, RELU, OUT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -518,10 +542,12 @@ cudaError_t dispatch_tc(const float *w, const float *bias, void *y, const TcPara
                         int out_f32, cudaStream_t s) {
 #define TG_TC_CASE(CI, CO)                                                              \
     if (cin == CI && cout == CO) {                                                      \
-        if (relu && out_f32) return run_tc<CI, CO, true, true>(w, bias, y, p, s);       \
-        if (relu) return run_tc<CI, CO, true, false>(w, bias, y, p, s);                 \
-        if (out_f32) return run_tc<CI, CO, false, true>(w, bias, y, p, s);              \
-        return run_tc<CI, CO, false, false>(w, bias, y, p, s);                          \
+        if (out_f32 == 2) return relu ? cudaErrorInvalidValue                           \
+                                      : run_tc<CI, CO, false, 2>(w, bias, y, p, s);     \
+        if (relu && out_f32) return run_tc<CI, CO, true, 1>(w, bias, y, p, s);          \
+        if (relu) return run_tc<CI, CO, true, 0>(w, bias, y, p, s);                     \
+        if (out_f32) return run_tc<CI, CO, false, 1>(w, bias, y, p, s);                 \
+        return run_tc<CI, CO, false, 0>(w, bias, y, p, s);                              \
     }
     TG_TC_CASE(16, 32)
     TG_TC_CASE(32, 32)
@@ -603,6 +629,14 @@ cudaError_t launch_conv3d_tc(const void *x, const float *w, const float *bias, v
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t set_tc_wait_test(int stall, long long budget_cycles) {
+    const long long b = budget_cycles > 0 ? budget_cycles : TC_WAIT_CYCLES;
+    const int st = stall ? 1 : 0;
+    cudaError_t e = cudaMemcpyToSymbol(g_tc_wait_cycles, &b, sizeof(b));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_stall, &st, sizeof(st));
+    return e;
 }
 
 // Reads and clears the tensor-core kernels' timeout flag (the caller has

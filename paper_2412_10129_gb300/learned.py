@@ -159,18 +159,22 @@ class _LGStep(torch.autograd.Function):
         saved = ctx.saved_tensors
         acts, ws = saved[:5], saved[5:]
         gxn = gxn.contiguous()
-        gy = tg.lg_pack(gxn, None, OUT_CH, so, 0.0)
+        # Every layer gradient travels as a BF16 pair hi + lo (FP32 precision
+        # on the BF16 tensor cores); activations and weights stay BF16.
+        hi, lo = tg.lg_pack_split(gxn, OUT_CH, so)
         dws, dbs = [None] * 5, [None] * 5
+        gin = None
         for li in range(4, -1, -1):
-            dws[li] = tg.conv3d_backward_weight(acts[li], gy)
-            dbs[li] = tg.conv3d_backward_bias(gy)
-            gin = tg.conv3d_backward_data(gy, ws[li])
+            dws[li] = tg.conv3d_backward_weight_split(acts[li], hi, lo)
+            dbs[li] = tg.conv3d_backward_bias_split(hi, lo)
+            gin = tg.conv3d_backward_data_split(hi, lo, ws[li])
             if li > 0:
-                tg.relu_backward(gin, acts[li], out=gin)
-            gy = gin
+                hi, lo = tg.grad_split(gin, acts[li])
+                del gin
+        del hi, lo
         gx = gxn.clone()
         gg = torch.empty_like(gxn)
-        tg.lg_unpack(gy, gx, gg, sx, sg, accumulate=True)
+        tg.lg_unpack_f32(gin, gx, gg, sx, sg, accumulate=True)
         tg.gradient(geo, gg, None, out=gx, accumulate=True)
         return (gx, None, None, *dws, *dbs)
 
