@@ -112,6 +112,14 @@ CASES = {
 }
 
 
+def bench_config(case, world):
+    """The `config` object both arms print for a workload."""
+    return {"workload": CASES[case][0], "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs (2.8 GB) exceed L2 (129 MB); no flush" if case == "clinical"
+            else "inputs (0.35 GB) exceed L2 (129 MB); no flush",
+            "step": "tg_cgls 1 iteration + tg_forward(siddon) + tg_fdk"}
+
+
 def make_inputs(case="clinical", seed=1):
     from paper_2412_10129_gb300 import inputs
     if case == "medium":
@@ -170,12 +178,19 @@ def replica_value(units_per_rank, steps, secs_max, world):
 # CPU FP64 oracle on a bounded sample of the workload.
 # ---------------------------------------------------------------------------
 
-def oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=96, seed=0):
+# The bounded oracle sample both CPU legs time: the interpolated FP of every
+# pixel of REF_FP_ANGLES angles and the matched BP (gather form) of
+# REF_BP_VOXELS random voxels over all angles.
+REF_FP_ANGLES = 1
+REF_BP_VOXELS = 32
+
+
+def oracle_sample(g, x, y, n_fp_angles=REF_FP_ANGLES, n_bp_voxels=REF_BP_VOXELS, seed=0):
     """Time the oracle: interpolated FP of every pixel of `n_fp_angles`
     angles, matched BP (gather form) of `n_bp_voxels` voxels over all angles.
+    Units are counted on the host in FP64 (no GPU library is loaded).
     Returns (units, seconds, description)."""
     import oracle
-    from paper_2412_10129_gb300 import tg
     rng = np.random.default_rng(seed)
     sub = g.subset(np.linspace(0, g.nAngles - 1, n_fp_angles).astype(int))
     rays = np.stack(np.meshgrid(np.arange(sub.nAngles), np.arange(g.nDetector[1]), np.arange(g.nDetector[0]),
@@ -186,11 +201,27 @@ def oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=96, seed=0):
     t1 = time.perf_counter()
     oracle.backproject_voxels(g, y, vox, "matched")
     t2 = time.perf_counter()
-    fp_units = tg.count_samples(sub, "interp") if _gpu_ok() else _count_samples_host(sub)
+    fp_units = _count_samples_host(sub)
     units = fp_units + n_bp_voxels * g.nAngles
     desc = (f"oracle interpolated FP of all {len(rays)} rays of {n_fp_angles} angle(s) ({fp_units} samples) + "
             f"matched BP of {n_bp_voxels} random voxels x {g.nAngles} angles")
     return units, t2 - t0, desc
+
+
+def cpu_baseline_line(g, x, y, min_seconds=10.0):
+    """cpu_baseline: the oracle sample repeated until at least `min_seconds`
+    of host time have been spent."""
+    units = 0
+    secs = 0.0
+    reps = 0
+    desc = ""
+    while secs < min_seconds or reps == 0:
+        u, t, desc = oracle_sample(g, x, y)
+        units += u
+        secs += t
+        reps += 1
+    return {"value": units / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{reps} x ({desc})"}
 
 
 def _gpu_ok():
@@ -246,12 +277,12 @@ def run_reference(args):
     g, x = make_inputs()
     y = inputs.random_projections(g.subset(np.arange(g.nAngles)), seed=3)
     for _ in range(args.warmup):
-        oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=32)
+        oracle_sample(g, x, y)
     units = 0
     secs = 0.0
     desc = ""
     for _ in range(args.steps):
-        u, s, desc = oracle_sample(g, x, y, n_fp_angles=1, n_bp_voxels=32)
+        u, s, desc = oracle_sample(g, x, y)
         units += u
         secs += s
     value = units / secs
@@ -259,7 +290,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample_per_step": desc},
+            "config": bench_config("clinical", world), "sample_per_step": desc,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -384,10 +415,7 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": CASES[args.case][0], "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs (2.8 GB) exceed L2 (129 MB); no flush",
-                       "step": "tg_cgls 1 iteration + tg_forward(siddon) + tg_fdk",
-                       "units_per_step": units_step},
+            "config": bench_config(args.case, world), "units_per_step": units_step,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
@@ -398,10 +426,7 @@ def run_gpu(args):
                       "fp_siddon_segments_per_s": s_siddon / t_sid, "bp_fdk_pairs_per_s": bp_pairs / t_bpf,
                       "fp_plus_bp_matched": (s_interp + bp_pairs) / (t_fp + t_bp)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        y_np = b_np
-        units_c, secs_c, desc = oracle_sample(g, x_np, y_np, n_fp_angles=2, n_bp_voxels=128)
-        line["cpu_baseline"] = {"value": units_c / secs_c, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": desc}
+        line["cpu_baseline"] = cpu_baseline_line(g, x_np, b_np)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -57,7 +57,7 @@ typedef enum {
     TG_ERR_GEOMETRY = 2,    /* non-positive sizes, DSD <= 0, DSO <= 0, ... */
     TG_ERR_OOM = 3,         /* scratch allocation failed */
     TG_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed */
-    TG_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    TG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (tg_device_status) */
     TG_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
 } tg_status;
 
@@ -139,21 +139,24 @@ tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngl
 
 /* tg_backproject for callers that cannot allocate device memory (the paper
  * has no counterpart: this is a deployment variant).  Some callers cannot
- * call cudaMalloc when they backproject -- code running while a CUDA graph
- * is built around it, hosts that fix their device memory budget at start-up,
- * latency-bound real-time paths -- so this call allocates nothing, neither
- * device nor host heap memory.  Same arguments and results as
- * tg_backproject, with these limits:
- *   - proj and vol must be device (or managed) memory; host buffers return
- *     TG_ERR_ARG (staging them would need an allocation);
+ * call cudaMalloc when they backproject -- a host process that reserves its
+ * device-memory budget at start-up and forbids allocation afterwards,
+ * real-time paths that cannot afford an allocator's latency or its failure
+ * -- so this call allocates nothing, neither device nor host heap memory.
+ * Same arguments and results as tg_backproject, with these limits:
+ *   - proj and vol must be device memory of the current device (or managed
+ *     memory); host buffers and other devices' buffers return TG_ERR_ARG
+ *     (staging them would need an allocation);
  *   - nAngles <= 4096 and batch <= 256, else TG_ERR_UNSUPPORTED;
  *   - its scratch (per-angle constants and one word per batch item, under
- *     1 MiB) is one static device array that every GPU loading the library
+ *     2 MiB) is one static device array that every GPU loading the library
  *     holds until the process exits.  The first call on a device looks the
  *     array's address up (cudaGetSymbolAddress) for that device; make that
- *     first call before any stream capture.  Every call reuses the same
- *     array, so calls that overlap on the GPU (other streams, other host
- *     threads) race: serialise them, e.g. on one stream. */
+ *     first call before any stream capture.  The per-angle constants reach
+ *     the array through kernel launches that carry them as parameters.
+ *     Every call reuses the same array, and it keeps the last call's
+ *     contents; calls that overlap on the GPU (other streams, other host
+ *     threads) race on it: serialise them, e.g. on one stream. */
 tg_status tg_backproject_noalloc(const tg_geometry *geo, const double *angles, int nAngles,
                                  const float *proj, float *vol, int method, int batch, void *stream);
 
@@ -253,8 +256,9 @@ tg_status tg_cgls(const tg_geometry *geo, const double *angles, int nAngles, con
  * TG_ERR_ARG before anything is launched. */
 
 /* y[v,o] = bias[o] + sum_{d in {-1,0,1}^3} sum_i x[v+d,i] w[d,o,i], zero
- * padding at each volume's faces, optional ReLU; y is BF16, or FP32 when
- * out_f32 != 0.  bias may be NULL.  n volumes of nz*ny*nx voxels each. */
+ * padding at each volume's faces, optional ReLU; y is BF16 (out_f32 == 0),
+ * FP32 (out_f32 == 1), or FP32 with the result added to y (out_f32 == 2,
+ * not with relu).  bias may be NULL.  n volumes of nz*ny*nx voxels each. */
 tg_status tg_conv3d_forward(const void *x, const float *w, const float *bias, void *y, int n, int nz, int ny,
                             int nx, int cin, int cout, int relu, int out_f32, void *stream);
 
@@ -302,6 +306,39 @@ tg_status tg_lg_unpack(const void *in, int channels, float *a, float *b, size_t 
 tg_status tg_lg_update(const float *x, const float *net, float *xnext, size_t nvox, int net_channels, float so,
                        void *stream);
 
+/* Gradients in FP32 precision on the BF16 tensor cores.  The network's
+ * weights and activations are BF16 (FP32 accumulation); its gradients are
+ * not, so the backward pass carries each layer gradient g as a pair of BF16
+ * tensors hi = bf16(g), lo = bf16(g - hi) (hi + lo = g to about 2^-17 of
+ * |g|) and applies each linear map to both halves, summing in FP32. */
+
+/* hi[i] = bf16(m g[i]), lo[i] = bf16(m g[i] - hi[i]) for count elements,
+ * m = (act[i] > 0) when act (BF16) is not NULL -- the ReLU backward of the
+ * layer whose input was act -- else 1. */
+tg_status tg_grad_split(const float *g, const void *act, void *hi, void *lo, size_t count, void *stream);
+
+/* The network's output gradient as a split pair: channel 0 of the
+ * [nvox][channels] BF16 tensors holds the split of s x[v], the other
+ * channels (channels = 8 or 16) hold zeros. */
+tg_status tg_lg_pack_split(const float *x, void *hi, void *lo, size_t nvox, int channels, float s, void *stream);
+
+/* tg_lg_unpack for an FP32 [nvox][channels] tensor. */
+tg_status tg_lg_unpack_f32(const float *in, int channels, float *a, float *b, size_t nvox, float sa, float sb,
+                           int accumulate, void *stream);
+
+/* tg_conv3d_backward_data of gy = gy_hi + gy_lo (BF16 pair), gx FP32
+ * [n][nz][ny][nx][cin] (overwritten). */
+tg_status tg_conv3d_backward_data_split(const void *gy_hi, const void *gy_lo, const float *w, float *gx, int n,
+                                        int nz, int ny, int nx, int cin, int cout, void *stream);
+
+/* tg_conv3d_backward_weight of gy = gy_hi + gy_lo (dw overwritten). */
+tg_status tg_conv3d_backward_weight_split(const void *x, const void *gy_hi, const void *gy_lo, float *dw, int n,
+                                          int nz, int ny, int nx, int cin, int cout, void *stream);
+
+/* tg_conv3d_backward_bias of gy = gy_hi + gy_lo (db overwritten). */
+tg_status tg_conv3d_backward_bias_split(const void *gy_hi, const void *gy_lo, float *db, size_t nvox, int cout,
+                                        void *stream);
+
 /* Waits for `stream`, then reports (and clears) the device-side wait flag
  * of the tensor-core kernels: TG_ERR_TIMEOUT when one of their bounded
  * waits gave up since the last call (their outputs are then invalid),
@@ -309,6 +346,36 @@ tg_status tg_lg_update(const float *x, const float *net, float *xnext, size_t nv
  * (producer, MMA and epilogue roles of the tcgen05 convolutions) never
  * spin without a limit; this is how a caller learns that a limit ran out. */
 tg_status tg_device_status(void *stream);
+
+/* Per-kernel timing (the paper has no counterpart; measurement support).
+ * While enabled, every launch of the kernel classes below is bracketed by
+ * two CUDA events on its stream; tg_kernel_timing_read waits for the
+ * recorded launches and returns the summed device time (ms) and the number
+ * of launches of one class since the last tg_kernel_timing call, which
+ * enables (enable != 0) or disables recording and clears the totals. */
+enum {
+    TG_KT_FP_INTERP = 0,   /* interpolated projector (TG_INTERP) */
+    TG_KT_FP_SIDDON = 1,   /* Siddon projector */
+    TG_KT_BP_MATCHED = 2,  /* matched transpose of TG_INTERP (brick scatter) */
+    TG_KT_BP_FDK = 3,      /* FDK-weighted backprojection */
+    TG_KT_BP_SIDDON = 4,   /* transpose of the Siddon projector */
+    TG_KT_FDK_FILTER = 5,  /* FDK row filter */
+    TG_KT_COUNT = 6
+};
+tg_status tg_kernel_timing(int enable);
+tg_status tg_kernel_timing_read(int kernel_class, double *ms, uint64_t *launches);
+
+/* Test hook of those bounded waits (the paper has no counterpart).  After
+ * a device synchronisation, sets the budget of each role's wait in the
+ * tensor-core convolutions to budget_cycles SM clocks (<= 0: the default,
+ * about two seconds) and, when stall != 0, makes every CTA's epilogue wait
+ * on a barrier that nothing arrives at: that wait runs out, the CTA sets
+ * the flag, its roles finish their own copies and MMAs, frees its tensor
+ * memory and returns, and the next tg_device_status reports
+ * TG_ERR_TIMEOUT (the convolution's output is then invalid).  Call again
+ * with (0, 0) to restore normal operation.  Process-wide; not for use
+ * while other threads launch convolutions. */
+tg_status tg_test_conv_wait(int stall, long long budget_cycles);
 
 /* MLEM (Sec. 2.1, Eq. 5; statistical methods): x <- x V A^T (b / (A x)),
  * V = 1/(A^T 1), the Kullback-Leibler / Poisson-likelihood counterpart of

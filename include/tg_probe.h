@@ -4,7 +4,8 @@
  * Measurement support, not part of the reconstruction path: the ceilings
  * against which the interpolated projector and its transpose are reported.
  * Their unit of work is a trilinear sample, eight voxels read from a 2x2x2
- * neighbourhood (32 bytes of FP32 data, two 2x2 texture gathers); the paper
+ * neighbourhood (32 bytes of FP32 data, two 2x2 texture gathers) or, in the
+ * transpose, eight contributions scattered into shared memory; the paper
  * (TIGRE v3, Sec. 2.5 on GPU acceleration) names no such rate, so these
  * calls measure it on the device at hand.
  *
@@ -36,6 +37,12 @@ int tgp_sector_gather(size_t bytes, int reps, double *gbs, double *ms_per_launch
  * *gathers_per_s: lane gathers per second. */
 int tgp_tex_gather(int nx, int ny, int nlayers, int coherent, int reps, double *gathers_per_s,
                    double *ms_per_launch);
+
+/* 32-bit integer atomic adds to a 64 KB shared-memory array, 1024-thread
+ * CTAs at full residency.  random == 0: the 32 lanes of a warp hit 32
+ * different banks (one wavefront per warp instruction); random != 0: each
+ * lane hits a random word.  *atomics_per_s: lane atomics per second. */
+int tgp_smem_atomic(int random, int reps, double *atomics_per_s, double *ms_per_launch);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,11 @@
 //                      of a warp on an 8 x 4 patch of neighbouring texel
 //                      footprints (the access pattern of a warp of rays in
 //                      the interpolated projector) or with every lane at a
-//                      random position.
+//                      random position; a small array stays in L1;
+//   tgp_smem_atomic    32-bit integer atomic adds to shared memory, either
+//                      with the 32 lanes of a warp on 32 different banks or
+//                      at random addresses of a 64 KB array (the scatter of
+//                      the matched backprojector's trilinear contributions).
 //
 // Every call allocates its own buffers, times `reps` launches with CUDA
 // events on a private stream after one warm-up launch and frees everything
@@ -90,6 +94,30 @@ __global__ void __launch_bounds__(256) k_tex_gather(cudaTextureObject_t tex, int
     if (acc == 1.2345e-30f) sink[0] = acc;
 }
 
+// Each thread adds 1 at `trips` x 8 shared-memory words: RANDOM picks
+// random words of the 16384-word array (eight per-thread offsets plus one
+// random shift per trip), else word lane + 32 m (bank = lane, conflict-free).
+template <bool RANDOM>
+__global__ void __launch_bounds__(1024) k_smem_atomic(int trips, unsigned *sink) {
+    constexpr unsigned WORDS = 16384;
+    extern __shared__ unsigned sm[];
+    for (unsigned i = threadIdx.x; i < WORDS; i += blockDim.x) sm[i] = 0u;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned s = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 0x9e3779b9u;
+    if (s == 0) s = 1;
+    unsigned off[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) off[j] = RANDOM ? xorshift(s) : (lane + 32u * (unsigned)(j * 61 + threadIdx.x / 32));
+    for (int t = 0; t < trips; ++t) {
+        const unsigned sh = RANDOM ? xorshift(s) : 32u * (unsigned)(t * 7);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&sm[(off[j] + sh) & (WORDS - 1u)], 1u);
+    }
+    __syncthreads();
+    if (sm[threadIdx.x] == 0xFFFFFFFFu) sink[0] = 1u;  // keeps the atomics (never true)
+}
+
 struct Timer {
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -154,6 +182,43 @@ int tgp_sector_gather(size_t bytes, int reps, double *gbs, double *ms_per_launch
         if (ms_per_launch) *ms_per_launch = ms / reps;
     }
     if (buf) cudaFree(buf);
+    if (sink) cudaFree(sink);
+    return (int)e;
+}
+
+int tgp_smem_atomic(int random, int reps, double *atomics_per_s, double *ms_per_launch) {
+    if (!atomics_per_s || reps <= 0) return (int)cudaErrorInvalidValue;
+    Timer t;
+    cudaError_t e = t.init();
+    unsigned *sink = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(unsigned));
+    const int threads = 1024, smem = 16384 * 4, trips = 512;
+    const void *fn = random ? (const void *)k_smem_atomic<true> : (const void *)k_smem_atomic<false>;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+    const int blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    auto launch = [&]() {
+        if (random)
+            k_smem_atomic<true><<<blocks, threads, smem, t.s>>>(trips, sink);
+        else
+            k_smem_atomic<false><<<blocks, threads, smem, t.s>>>(trips, sink);
+        return cudaGetLastError();
+    };
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(t.e0, t.s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(t.e1, t.s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t.e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.e0, t.e1);
+    if (e == cudaSuccess) {
+        const double n = (double)blocks * threads * trips * 8.0 * reps;  // lane atomics
+        *atomics_per_s = n / (ms * 1e-3);
+        if (ms_per_launch) *ms_per_launch = ms / reps;
+    }
     if (sink) cudaFree(sink);
     return (int)e;
 }

@@ -28,7 +28,10 @@
 //
 // TG_FDK_WEIGHT is the FDK backprojection (Sec. 2.1, direct methods):
 //     x_j = (pi / nAngles) sum_a (DSO / L_ja)^2 bilinear(p_a, u_ja, v_ja).
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 
 #include "tg_internal.cuh"
 #include "tg_ray.cuh"
@@ -424,6 +427,271 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
 }
 
+// ---- compact-record variant ---------------------------------------------
+// The same scatter with 8-byte ray records (y is read again when a lane
+// takes the ray), so that a list holds RAYCAP8 rays, and two options:
+//   NT  threads per CTA (512 or 1024; each owns BX*BY*BZ/NT voxels),
+//   OG  the owned voxels' FP32 sums live in the output volume instead of
+//       registers (BP_STORE / BP_STORE_NORM: the output is the accumulator),
+//   LF  long rays first: a chunk lists rays of at least LONG_RAY samples
+//       from the front of the list and shorter ones from the back, so the
+//       lane queue hands out the long rays first and the chunk's tail is
+//       made of short ones.
+// Record: iuv = iu | iv << 16; kk = ka | (kc - ka) << 20 | class << 31
+// (ka < 2^20, kc - ka < 2^11: checked on the host).
+struct RayRec8 {
+    unsigned int iuv;
+    unsigned int kk;
+};
+constexpr int RAYCAP8 = 2048;
+constexpr int LONG_RAY = 32;
+constexpr int MATCHED8_SMEM = 2 * ACC_WORDS * 4 + RAYCAP8 * (int)sizeof(RayRec8);
+static_assert(MATCHED8_SMEM <= 232448 - 512, "shared memory of one CTA");
+
+template <bool PAR>
+__device__ __forceinline__ bool region_ray8(const Angle &A, const Grid &g, float yraw, int iu, int iv, bool edge,
+                                            float lox, float loy, float loz, float hix, float hiy, float hiz,
+                                            float ybig, RayRec8 &rec, int &len) {
+    if (yraw == 0.f) return false;
+    Ray r;
+    int kb0 = 0, kb1 = 0x7fffffff;
+    if (edge) {
+        if (!ray_setup_outlined<PAR>(A, g, iu, iv, r)) return false;
+        kb0 = r.k0;
+        kb1 = r.k1;
+    } else {
+        float Ld;
+        ray_frame<PAR>(A, g, iu, iv, r, Ld);
+    }
+    float klo = (float)kb0, khi = (float)kb1;
+    const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
+    const float lo[3] = {lox, loy, loz}, hi[3] = {hix, hiy, hiz};
+    const float kr = (float)r.kr;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (gv[ax] != 0.f) {
+            const float ia = 1.f / gv[ax];
+            const float ka = fmaf(lo[ax] - sv[ax], ia, kr), kc = fmaf(hi[ax] - sv[ax], ia, kr);
+            klo = fmaxf(klo, fminf(ka, kc));
+            khi = fminf(khi, fmaxf(ka, kc));
+        } else if (sv[ax] < lo[ax] || sv[ax] >= hi[ax]) {
+            return false;
+        }
+    }
+    if (!(khi >= klo)) return false;
+    const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
+    if (ka > kc) return false;
+    const bool big = fabsf(yraw) > ybig;
+    rec.iuv = (unsigned int)iu | ((unsigned int)iv << 16);
+    rec.kk = (unsigned int)ka | ((unsigned int)(kc - ka) << 20) | (big ? 0x80000000u : 0u);
+    len = kc - ka + 1;
+    return true;
+}
+
+template <int MODE, bool PAR, int NT, bool OG, bool LF>
+__device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, float *__restrict__ vb,
+                                                  const Angle *__restrict__ angles, const Grid &g,
+                                                  const BpEpilogue &ep, float gmax, int bx, int by, int bz) {
+    static_assert(!OG || MODE == BP_STORE || MODE == BP_STORE_NORM, "global sums use the output as accumulator");
+    constexpr int NW = NT / 32;                 // warps
+    constexpr int YR = BY / NW;                 // owned y rows per thread
+    constexpr int OWNN = BX * BY * BZ / NT;     // owned voxels per thread
+    static_assert(NW * YR == BY && OWNN == YR * BZ, "owned-voxel map");
+    extern __shared__ unsigned int acc[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
+    const float lox = (float)(x0 - 1), loy = (float)(y0 - 1), loz = (float)(z0 - 1);
+    const float hix = (float)(x0 + BX), hiy = (float)(y0 + BY), hiz = (float)(z0 + BZ);
+    const bool edge = x0 == 0 || y0 == 0 || z0 == 0 || x0 + BX >= g.nx || y0 + BY >= g.ny || z0 + BZ >= g.nz;
+    unsigned int *acc_f = acc + ACC_WORDS;
+    RayRec8 *rays = reinterpret_cast<RayRec8 *>(acc + 2 * ACC_WORDS);
+    __shared__ int s_cnt[3];  // long rays listed, rays handed out, short rays listed
+    const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
+    const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
+    const float inv_scale = scale > 0.f ? 1.f / scale : 0.f;
+    const float scale_f = FINE * scale, inv_scale_f = inv_scale * (1.f / FINE);
+    const float ybig = gmax * (1.f / FINE);
+    const int obase = RIM * PP + (warp + RIM) * PX + lane + RIM;
+    const int ox = x0 - RIM, oy = y0 - RIM, oz = z0 - RIM;
+    float own[OG ? 1 : OWNN];
+#pragma unroll
+    for (int j = 0; j < (OG ? 1 : OWNN); ++j) own[j] = 0.f;
+    for (int i = tid; i < 2 * ACC_WORDS; i += NT) acc[i] = 0u;
+    __syncthreads();
+    bool first = true;
+    for (int a0 = 0; a0 < g.nA; a0 += FLUSH) {
+        const int a1 = min(a0 + FLUSH, g.nA);
+        for (int a = a0; a < a1; ++a) {
+            const Angle &A = angles[a];
+            float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float px = (((q & 1) ? hix : lox) + 0.5f - 0.5f * g.nx) * g.dx;
+                const float py = (((q & 2) ? hiy : loy) + 0.5f - 0.5f * g.ny) * g.dy;
+                const float pz = (((q & 4) ? hiz : loz) + 0.5f - 0.5f * g.nz) * g.dz;
+                const float L = fmaf(pz, A.n[2], fmaf(py, A.n[1], px * A.n[0])) - A.Sn;
+                const float Au = fmaf(pz, A.eu[2], fmaf(py, A.eu[1], px * A.eu[0])) - A.Seu;
+                const float Av = fmaf(pz, A.ev[2], fmaf(py, A.ev[1], px * A.ev[0])) - A.Sev;
+                const float iL = 1.f / L;
+                const float fu = fmaf(A.Ku * Au, iL, A.cu), fv = fmaf(A.Kv * Av, iL, A.cv);
+                umin = fminf(umin, fu);
+                umax = fmaxf(umax, fu);
+                vmin = fminf(vmin, fv);
+                vmax = fmaxf(vmax, fv);
+            }
+            const int u0 = max((int)ceilf(umin - 1e-3f), 0), u1 = min((int)floorf(umax + 1e-3f), g.nu - 1);
+            const int v0 = max((int)ceilf(vmin - 1e-3f), 0), v1 = min((int)floorf(vmax + 1e-3f), g.nv - 1);
+            if (u1 < u0 || v1 < v0) continue;
+            const float *pa = pb + (size_t)a * g.nv * g.nu;
+            const int ntu = (u1 - u0 + 32) >> 5, ntv = (v1 - v0 + 16) >> 4;
+            const int ncand = ntu * ntv * 16 * 32;
+            for (int c0 = 0; c0 < ncand;) {
+                if (tid == 0) {
+                    s_cnt[0] = 0;
+                    s_cnt[1] = 0;
+                    s_cnt[2] = 0;
+                }
+                __syncthreads();
+                while (c0 < ncand) {
+                    const int cand = c0 + tid;
+                    bool keep = false;
+                    int len = 0;
+                    RayRec8 rec;
+                    if (cand < ncand) {
+                        const int task = cand >> 5, slot = cand & 31;
+                        const int ph = task & 15, tile = task >> 4;
+                        const int iu = u0 + (tile % ntu) * 32 + (slot & 7) * 4 + (ph & 3);
+                        const int iv = v0 + (tile / ntu) * 16 + (slot >> 3) * 4 + (ph >> 2);
+                        if (iu <= u1 && iv <= v1)
+                            keep = region_ray8<PAR>(A, g, __ldg(pa + (size_t)iv * g.nu + iu), iu, iv, edge, lox, loy,
+                                                    loz, hix, hiy, hiz, ybig, rec, len);
+                    }
+                    if (LF) {
+                        const bool lg = keep && len >= LONG_RAY;
+                        const unsigned ml = __ballot_sync(0xffffffffu, lg);
+                        const unsigned ms = __ballot_sync(0xffffffffu, keep && !lg);
+                        int bl = 0, bs = 0;
+                        if (lane == 0) {
+                            if (ml) bl = atomicAdd(&s_cnt[0], __popc(ml));
+                            if (ms) bs = atomicAdd(&s_cnt[2], __popc(ms));
+                        }
+                        bl = __shfl_sync(0xffffffffu, bl, 0);
+                        bs = __shfl_sync(0xffffffffu, bs, 0);
+                        const unsigned below = (1u << lane) - 1u;
+                        if (lg) rays[bl + __popc(ml & below)] = rec;
+                        else if (keep) rays[RAYCAP8 - 1 - (bs + __popc(ms & below))] = rec;
+                    } else {
+                        const unsigned m = __ballot_sync(0xffffffffu, keep);
+                        int base = 0;
+                        if (lane == 0 && m) base = atomicAdd(&s_cnt[0], __popc(m));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (keep) rays[base + __popc(m & ((1u << lane) - 1u))] = rec;
+                    }
+                    c0 += NT;
+                    __syncthreads();
+                    if (s_cnt[0] + s_cnt[2] > RAYCAP8 - NT) break;
+                }
+                const int nl = s_cnt[0], nr = s_cnt[0] + s_cnt[2];
+                int k = 1, kc = 0;
+                float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                unsigned int *accc = acc;
+                bool live = true;
+                while (true) {
+                    const bool need = live && k > kc;
+                    const unsigned m = __ballot_sync(0xffffffffu, need);
+                    if (m) {
+                        const int lead = __ffs(m) - 1;
+                        int base = 0;
+                        if (lane == lead) base = atomicAdd(&s_cnt[1], __popc(m));
+                        base = __shfl_sync(0xffffffffu, base, lead);
+                        if (need) {
+                            const int idx = base + __popc(m & ((1u << lane) - 1u));
+                            if (idx < nr) {
+                                const RayRec8 rr = rays[idx < nl ? idx : RAYCAP8 - 1 - (idx - nl)];
+                                const int iu = (int)(rr.iuv & 0xffffu), iv = (int)(rr.iuv >> 16);
+                                Ray q;
+                                float Ld;
+                                ray_frame<PAR>(A, g, iu, iv, q, Ld);
+                                gx = q.gx;
+                                gy = q.gy;
+                                gz = q.gz;
+                                sx = q.sx;
+                                sy = q.sy;
+                                sz = q.sz;
+                                const bool big = (rr.kk >> 31) != 0;
+                                ys = __ldg(pa + (size_t)iv * g.nu + iu) * (big ? scale : scale_f);
+                                const int ka = (int)(rr.kk & 0xfffffu);
+                                k = ka - q.kr;
+                                kc = ka + (int)((rr.kk >> 20) & 0x7ffu) - q.kr;
+                                accc = big ? acc : acc_f;
+                            } else {
+                                live = false;
+                            }
+                        }
+                    }
+                    if (!__any_sync(0xffffffffu, live)) break;
+                    if (!live) continue;
+                    scatter_sample<false>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
+                    scatter_sample<false>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
+                    k += 2;
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < OWNN; ++j) {
+            const int o = obase + (j / YR) * PP + (j % YR) * NW * PX;
+            const int v = (int)acc[o], vf = (int)acc_f[o];
+            acc[o] = 0u;
+            acc_f[o] = 0u;
+            const float add = fmaf((float)v, inv_scale, (float)vf * inv_scale_f);
+            if (OG) {
+                const int ix = x0 + lane, iy = y0 + warp + NW * (j % YR), iz = z0 + j / YR;
+                if (ix < g.nx && iy < g.ny && iz < g.nz) {
+                    float *dst = vb + ((size_t)iz * g.ny + iy) * g.nx + ix;
+                    *dst = (first ? 0.f : *dst) + add;
+                }
+            } else {
+                own[j] += add;
+            }
+        }
+        first = false;
+        __syncthreads();
+    }
+    double part = 0.0;
+#pragma unroll
+    for (int j = 0; j < OWNN; ++j) {
+        const int ix = x0 + lane, iy = y0 + warp + NW * (j % YR), iz = z0 + j / YR;
+        const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
+        const size_t widx = ok ? ((size_t)iz * g.ny + iy) * g.nx + ix : 0;
+        const float sum = OG ? (ok ? (first ? 0.f : vb[widx]) : 0.f) : own[OG ? 0 : j];
+        if (MODE == BP_STORE_NORM) {
+            const float v = ep.scale * sum;
+            if (ok) {
+                vb[widx] = v;
+                part += (double)v * (double)v;
+            }
+        } else {
+            bp_epilogue<MODE>(sum, ok, widx, widx, ep, vb, 0);
+        }
+    }
+    if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
+}
+
+template <int MODE, bool PAR, int NT, bool OG, bool LF>
+__global__ void __launch_bounds__(NT, 1)
+    k_bp_matched8(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
+                  BpEpilogue ep, int nbx, int nby) {
+    const int bl = blockIdx.x, b = blockIdx.y;
+    BpEpilogue e = ep;
+    if (e.norm) e.norm += b;
+    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    bp_matched_brick8<MODE, PAR, NT, OG, LF>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
+                                             __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby,
+                                             bl / (nbx * nby));
+}
+
 template <int MODE, bool F32, bool PAR>
 __global__ void __launch_bounds__(MT, 1)
     k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
@@ -555,6 +823,38 @@ cudaError_t launch_matched_t(dim3 grid, const float *proj, float *vol, const Ang
     return cudaSuccess;
 }
 
+template <int MODE, int NT, bool OG, bool LF>
+cudaError_t launch_matched8_t(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
+                              const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
+    auto kern = k_bp_matched8<MODE, false, NT, OG, LF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MATCHED8_SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, MATCHED8_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
+    return cudaSuccess;
+}
+
+// Compact-record kernels (experiment selection by TG_BP_IMPL); returns
+// cudaErrorNotSupported when the request stays with k_bp_matched.
+template <int MODE>
+cudaError_t launch_matched8(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
+                            const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
+    const char *impl = getenv("TG_BP_IMPL");
+    if (!impl || g.parallel || ep.fp32_acc) return cudaErrorNotSupported;
+    const double dmin = fmin(fmin(g.dx, g.dy), g.dz);
+    const double chord = sqrt((double)(RX * RX) * g.dx * g.dx + (double)(RY * RY) * g.dy * g.dy +
+                              (double)(RZ * RZ) * g.dz * g.dz) / (double)g.delta + 2.0;
+    if (!(g.kmax < 1048000.f) || !(chord < 2000.0) || dmin <= 0.0) return cudaErrorNotSupported;
+    const std::string v(impl);
+    if (v == "c512") return launch_matched8_t<MODE, 512, false, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "c512lf") return launch_matched8_t<MODE, 512, false, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "c1024") return launch_matched8_t<MODE, 1024, false, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "c1024lf") return launch_matched8_t<MODE, 1024, false, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "g512lf") return launch_matched8_t<MODE, 512, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "g1024") return launch_matched8_t<MODE, 1024, true, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "g1024lf") return launch_matched8_t<MODE, 1024, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    return cudaErrorNotSupported;
+}
+
 template <int MODE, bool F32>
 cudaError_t launch_matched(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
                            const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
@@ -582,6 +882,16 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
         }
         dim3 grid((unsigned)(nbx * nby * nbz), batch);
         const bool f32 = ep.fp32_acc != 0;
+        KernelTimer kt(TG_KT_BP_MATCHED, s);
+        if (mode == BP_STORE || mode == BP_STORE_NORM) {
+            e = mode == BP_STORE ? launch_matched8<BP_STORE>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                                 : launch_matched8<BP_STORE_NORM>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+            if (e == cudaSuccess) {
+                count_launch();
+                return cudaGetLastError();
+            }
+            if (e != cudaErrorNotSupported) return e;
+        }
         switch (mode) {
             case BP_STORE:
                 e = f32 ? launch_matched<BP_STORE, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
@@ -606,6 +916,7 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
         const int nzc = (g.nz + ZC - 1) / ZC;
         dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8, nzc * batch);
         if ((long long)nzc * batch > 65535) return cudaErrorInvalidConfiguration;
+        KernelTimer kt(TG_KT_BP_FDK, s);
         switch (mode) {
             case BP_STORE: k_bp_fdk<BP_STORE><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;
             case BP_SIRT: k_bp_fdk<BP_SIRT><<<grid, block, 0, s>>>(proj, vol, d_angles, g, ep, nzc); break;

@@ -224,6 +224,7 @@ cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const FdkAng
     if (threads > 256) threads = 256;
     dim3 grid(g.nv, g.nA, batch);
     cudaError_t e;
+    KernelTimer kt(TG_KT_FDK_FILTER, s);
     if (S == 2) {
         e = cudaFuncSetAttribute(k_fdk_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

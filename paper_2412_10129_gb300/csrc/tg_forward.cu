@@ -597,6 +597,7 @@ cudaError_t launch_siddon_scatter(const Grid &g, const Angle *d_angles, const fl
     if (g.nA == 0 || batch == 0) return cudaSuccess;
     const int nub = (g.nu + BU - 1) / BU, nvb = (g.nv + BV - 1) / BV;
     if ((long long)nvb * batch > 65535 || g.nA > 65535) return cudaErrorInvalidConfiguration;
+    KernelTimer kt(TG_KT_BP_SIDDON, s);
     if (g.parallel)
         k_bp_siddon_scatter<true><<<dim3(nub, g.nA, nvb * batch), 256, 0, s>>>(proj, out, d_angles, g, scale, nvb);
     else
@@ -631,6 +632,7 @@ cudaError_t launch_forward_t(int method, const Grid &g, const Angle *d_angles, c
             e = copy_to_texture(tc, vol + (size_t)b0 * nvox, gc, s);
             if (e != cudaSuccess) return e;
             dim3 grid1(nub, g.nA, nvb * nb);
+            KernelTimer kt(TG_KT_FP_INTERP, s);
             switch (mode) {
                 case FP_STORE: k_fp_interp_tex<FP_STORE, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
                 case FP_RESID_W: k_fp_interp_tex<FP_RESID_W, PAR><<<grid1, block, 0, s>>>(tc.tex, proj, d_angles, g, ep, nvb, b0); break;
@@ -646,6 +648,7 @@ cudaError_t launch_forward_t(int method, const Grid &g, const Angle *d_angles, c
         return cudaSuccess;
     } else if (method == TG_INTERP) {
         // volumes beyond the layered-texture limits read global memory
+        KernelTimer kt(TG_KT_FP_INTERP, s);
         switch (mode) {
             case FP_STORE: k_fp_interp<FP_STORE, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             case FP_RESID_W: k_fp_interp<FP_RESID_W, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
@@ -655,6 +658,7 @@ cudaError_t launch_forward_t(int method, const Grid &g, const Angle *d_angles, c
             default: return cudaErrorInvalidValue;
         }
     } else if (method == TG_SIDDON) {
+        KernelTimer kt(TG_KT_FP_SIDDON, s);
         switch (mode) {
             case FP_STORE: k_fp_siddon<FP_STORE, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;
             case FP_RESID_W: k_fp_siddon<FP_RESID_W, PAR><<<grid, block, 0, s>>>(vol, proj, d_angles, g, ep, nvb); break;

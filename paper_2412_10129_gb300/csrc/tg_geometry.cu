@@ -282,7 +282,7 @@ void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles,
     const double h[3] = {0.5 * geo->nVoxel[0] * geo->dVoxel[0] + geo->dVoxel[0],
                          0.5 * geo->nVoxel[1] * geo->dVoxel[1] + geo->dVoxel[1],
                          0.5 * geo->nVoxel[2] * geo->dVoxel[2] + geo->dVoxel[2]};
-    double mag = 0.0, obl = 1.0;
+    double mag = 0.0, obl = 1.0, lmax = 0.0;
     for (int a = 0; a < nAngles; ++a) {
         Frame f = frame(geo, angles, a);
         const double DSn = (f.D[0] - f.S[0]) * f.n[0] + (f.D[1] - f.S[1]) * f.n[1] + (f.D[2] - f.S[2]) * f.n[2];
@@ -290,6 +290,7 @@ void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles,
             const double DS[3] = {f.D[0] - f.S[0], f.D[1] - f.S[1], f.D[2] - f.S[2]};
             const double o = sqrt(dot(DS, DS)) / DSn;
             if (o > obl) obl = o;
+            if (sqrt(dot(DS, DS)) > lmax) lmax = sqrt(dot(DS, DS));
             if (mag < 1.0) mag = 1.0;
             continue;
         }
@@ -302,6 +303,7 @@ void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles,
                 r2 += c * c;
             }
             if (sqrt(r2) / DSn > obl) obl = sqrt(r2) / DSn;
+            if (sqrt(r2) > lmax) lmax = sqrt(r2);
         }
         for (int q = 0; q < 8; ++q) {
             double depth = 0.0;
@@ -312,6 +314,7 @@ void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles,
     const double per_ray = 2.0 * sqrt(3.0) * dmax / g.delta64 + 1.0;
     const double width = 1.1 * obl * 2.0 * sqrt(3.0) * dmax * mag / pmin + 2.0;
     g.wbound = (float)(per_ray * width * width);
+    g.kmax = (float)(lmax / g.delta64 + 2.0);
 }
 
 Grid make_grid(const tg_geometry *geo, int nAngles) {

@@ -87,6 +87,9 @@ struct Grid {
     // Upper bound of the summed trilinear weights one voxel can receive from
     // one projection (matched backprojector fixed-point range).
     float wbound;
+    // Upper bound of any ray's last sample index |P - S| / delta (set with
+    // wbound; sizes the matched backprojector's compact ray records).
+    float kmax;
     float sdh[3], sdl[3];  // delta / d per axis, double-float
     int parallel;          // parallel beam (tg_geometry.parallel)
 };
@@ -140,6 +143,21 @@ void set_weight_bound(const tg_geometry *geo, const double *angles, int nAngles,
 // Launch bookkeeping (tg_api.cu).
 void count_launch(uint64_t n = 1);
 
+// Brackets the launches issued during its lifetime with CUDA events when
+// tg_kernel_timing is enabled (tg_timing.cu); `cls` is a TG_KT_* class.
+class KernelTimer {
+  public:
+    KernelTimer(int cls, cudaStream_t s);
+    ~KernelTimer();
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+  private:
+    int cls_;
+    cudaStream_t s_;
+    cudaEvent_t e0_ = nullptr, e1_ = nullptr;
+};
+
 // Kernel launchers (each returns cudaGetLastError()).
 cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, const float *vol,
                            float *proj, int batch, int mode, const FpEpilogue &ep, cudaStream_t s);
@@ -173,7 +191,8 @@ cudaError_t launch_fdk_filter(const Grid &g, const Angle *d_angles, const FdkAng
                               int filter, int weights, float Delta, const float *proj, float *out, int batch,
                               cudaStream_t s);
 
-// Learned-gradient network kernels (tg_conv.cu).
+// Learned-gradient network kernels (tg_conv.cu).  out_f32: 0 = BF16 output,
+// 1 = FP32 output, 2 = FP32 added to y (no ReLU).
 cudaError_t launch_conv3d(const void *x, const float *w, const float *bias, void *y, int N, int Z, int Y, int X,
                           int cin, int cout, int relu, int out_f32, cudaStream_t s);
 cudaError_t launch_conv3d_ragged(const void *x, const float *w, const float *bias, void *y, const int *dims,
@@ -185,10 +204,18 @@ cudaError_t launch_conv3d_tc(const void *x, const float *w, const float *bias, v
 cudaError_t launch_conv3d_tc_ragged(const void *x, const float *w, const float *bias, void *y, const int *dims,
                                     int nvol, int cin, int cout, int relu, int out_f32, cudaStream_t s);
 cudaError_t read_tc_error(int *flag);
+// Test hook of the tensor-core kernels' bounded waits (tg_test_conv_wait).
+cudaError_t set_tc_wait_test(int stall, long long budget_cycles);
+// zero: clear dw first (else the gradient is added to it).
 cudaError_t launch_conv3d_wgrad(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, int cin,
-                                int cout, cudaStream_t s);
+                                int cout, cudaStream_t s, int zero = 1);
 cudaError_t launch_flip_weights(const float *w, float *wb, int cin, int cout, cudaStream_t s);
-cudaError_t launch_bias_grad(const void *gy, float *db, size_t nvox, int cout, cudaStream_t s);
+cudaError_t launch_bias_grad(const void *gy, float *db, size_t nvox, int cout, cudaStream_t s, int zero = 1);
+// Split gradients (hi + lo BF16 pairs, see k_grad_split in tg_conv.cu).
+cudaError_t launch_grad_split(const float *g, const void *act, void *hi, void *lo, size_t n, cudaStream_t s);
+cudaError_t launch_lg_pack_split(const float *a, void *hi, void *lo, size_t nvox, int C, float sa, cudaStream_t s);
+cudaError_t launch_lg_unpack_f32(const float *in, int C, float *a, float *b, size_t nvox, float sa, float sb,
+                                 int accumulate, cudaStream_t s);
 cudaError_t launch_relu_backward(const void *g, const void *act, void *out, size_t n, cudaStream_t s);
 cudaError_t launch_lg_pack(const float *a, const float *b, void *out, size_t nvox, int C, float sa, float sb,
                            cudaStream_t s);

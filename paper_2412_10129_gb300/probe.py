@@ -22,6 +22,7 @@ def load():
         D = ctypes.POINTER(ctypes.c_double)
         lib.tgp_sector_gather.argtypes = [ctypes.c_size_t, ctypes.c_int, D, D]
         lib.tgp_tex_gather.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
+        lib.tgp_smem_atomic.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
         _lib = lib
     return _lib
 
@@ -47,12 +48,24 @@ def tex_gather(nx: int, ny: int, nlayers: int, coherent: bool, reps: int = 10) -
             "coherent": bool(coherent), "gathers_per_s": rate.value, "ms_per_launch": ms.value}
 
 
+def smem_atomic(random: bool, reps: int = 10) -> dict:
+    """32-bit shared-memory integer atomics: conflict-free or random words."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    rc = load().tgp_smem_atomic(1 if random else 0, int(reps), ctypes.byref(rate), ctypes.byref(ms))
+    if rc:
+        raise RuntimeError(f"tgp_smem_atomic failed: cudaError {rc}")
+    return {"random": bool(random), "atomics_per_s": rate.value, "ms_per_launch": ms.value}
+
+
 def gather_rates() -> dict:
     """The rates a projector roofline needs: L2-resident (64 MiB) and
-    HBM-resident (2 GiB) random sector gathers, and warp-coherent and random
-    texture gathers from an L2-resident 64 MiB layered array."""
+    HBM-resident (2 GiB) random sector gathers; warp-coherent and random
+    texture gathers from an L2-resident 64 MiB layered array and from an
+    L1-resident 64 KB one; conflict-free and random shared-memory atomics."""
     return {"l2_sector": sector_gather(64 << 20), "hbm_sector": sector_gather(2 << 30, reps=3),
-            "tex_coherent": tex_gather(512, 512, 64, True), "tex_random": tex_gather(512, 512, 64, False)}
+            "tex_coherent": tex_gather(512, 512, 64, True), "tex_random": tex_gather(512, 512, 64, False),
+            "tex_coherent_l1": tex_gather(64, 64, 4, True), "tex_random_l1": tex_gather(64, 64, 4, False),
+            "smem_atomic_conflict_free": smem_atomic(False), "smem_atomic_random": smem_atomic(True)}
 
 
 if __name__ == "__main__":

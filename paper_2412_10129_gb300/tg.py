@@ -108,7 +108,17 @@ def load():
             "tg_lg_unpack": [_VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, ctypes.c_float, ctypes.c_float,
                              ctypes.c_int, _VP],
             "tg_lg_update": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_float, _VP],
+            "tg_grad_split": [_VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+            "tg_lg_pack_split": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_float, _VP],
+            "tg_lg_unpack_f32": [_VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_int, _VP],
+            "tg_conv3d_backward_data_split": [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP],
+            "tg_conv3d_backward_weight_split": [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP],
+            "tg_conv3d_backward_bias_split": [_VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int, _VP],
             "tg_device_status": [_VP],
+            "tg_test_conv_wait": [ctypes.c_int, ctypes.c_longlong],
+            "tg_kernel_timing": [ctypes.c_int],
+            "tg_kernel_timing_read": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
             "tg_forward_batched": [G, ctypes.POINTER(_DP), ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP, _VP],
             "tg_backproject_batched": [G, ctypes.POINTER(_DP), ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP,
                                        _VP],
@@ -527,6 +537,31 @@ def device_status(stream=None) -> None:
     _check("tg_device_status", load().tg_device_status(st))
 
 
+def test_conv_wait(stall: bool, budget_cycles: int = 0) -> None:
+    """tg_test_conv_wait: test hook of the tensor-core convolutions' bounded
+    waits (budget in SM clocks, 0 = default; ``stall`` makes their epilogue
+    wait on a barrier that nothing arrives at)."""
+    _check("tg_test_conv_wait", load().tg_test_conv_wait(1 if stall else 0, int(budget_cycles)))
+
+
+KERNEL_CLASSES = {"fp_interp": 0, "fp_siddon": 1, "bp_matched": 2, "bp_fdk": 3, "bp_siddon": 4, "fdk_filter": 5}
+
+
+def kernel_timing(enable: bool) -> None:
+    """tg_kernel_timing: start (or stop) recording per-kernel launch times; clears the totals."""
+    _check("tg_kernel_timing", load().tg_kernel_timing(1 if enable else 0))
+
+
+def kernel_timing_read() -> dict:
+    """tg_kernel_timing_read for every class: {name: (total ms, launches)}."""
+    out = {}
+    for name, cls in KERNEL_CLASSES.items():
+        ms, n = ctypes.c_double(), ctypes.c_uint64()
+        _check("tg_kernel_timing_read", load().tg_kernel_timing_read(cls, ctypes.byref(ms), ctypes.byref(n)))
+        out[name] = (ms.value, int(n.value))
+    return out
+
+
 def launch_count() -> int:
     """Kernel launches libtg has issued in this process."""
     return int(load().tg_launch_count())
@@ -557,19 +592,24 @@ def _cs(t, stream):
     return _stream(t, stream)
 
 
-def conv3d(x, w, bias=None, relu: bool = False, out_f32: bool = False, out=None, stream=None):
-    """tg_conv3d_forward: x [n, nz, ny, nx, cin] bf16 -> [n, nz, ny, nx, cout]."""
+def conv3d(x, w, bias=None, relu: bool = False, out_f32: bool = False, out=None, accumulate: bool = False,
+           stream=None):
+    """tg_conv3d_forward: x [n, nz, ny, nx, cin] bf16 -> [n, nz, ny, nx, cout]
+    (FP32 with ``out_f32``; ``accumulate`` adds the result to the FP32 ``out``)."""
     torch = _torch()
     n, nz, ny, nx, cin = x.shape
     cout = int(w.shape[1])
     if tuple(w.shape) != (27, cout, cin):
         raise ValueError("weights must be [27, cout, cin]")
+    if accumulate and (out is None or relu):
+        raise ValueError("accumulate needs an FP32 out and no ReLU")
+    f32 = bool(out_f32) or bool(accumulate)
     if out is None:
-        out = torch.empty((n, nz, ny, nx, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device=x.device)
+        out = torch.empty((n, nz, ny, nx, cout), dtype=torch.float32 if f32 else torch.bfloat16, device=x.device)
     _check("tg_conv3d_forward", load().tg_conv3d_forward(
         _dptr(x, torch.bfloat16), _dptr(w, torch.float32), None if bias is None else _dptr(bias, torch.float32),
-        _dptr(out, torch.float32 if out_f32 else torch.bfloat16), n, nz, ny, nx, cin, cout, int(bool(relu)),
-        int(bool(out_f32)), _cs(x, stream)))
+        _dptr(out, torch.float32 if f32 else torch.bfloat16), n, nz, ny, nx, cin, cout, int(bool(relu)),
+        2 if accumulate else int(f32), _cs(x, stream)))
     return out
 
 
@@ -657,6 +697,88 @@ def lg_unpack(t, a, b=None, sa: float = 1.0, sb: float = 1.0, accumulate: bool =
         None if b is None else _dptr(b, torch.float32), a.numel(), float(sa), float(sb), int(bool(accumulate)),
         _cs(t, stream)))
     return a
+
+
+def grad_split(g, act=None, out=None, stream=None):
+    """tg_grad_split: FP32 gradient g -> (hi, lo) bf16 with hi + lo = m g,
+    m the ReLU mask act > 0 (1 without ``act``)."""
+    torch = _torch()
+    if out is None:
+        out = (torch.empty(g.shape, dtype=torch.bfloat16, device=g.device),
+               torch.empty(g.shape, dtype=torch.bfloat16, device=g.device))
+    hi, lo = out
+    if act is not None and act.shape != g.shape:
+        raise ValueError("act must have the shape of g")
+    _check("tg_grad_split", load().tg_grad_split(
+        _dptr(g, torch.float32), None if act is None else _dptr(act, torch.bfloat16), _dptr(hi, torch.bfloat16),
+        _dptr(lo, torch.bfloat16), g.numel(), _cs(g, stream)))
+    return hi, lo
+
+
+def lg_pack_split(x, channels: int, s: float = 1.0, stream=None):
+    """tg_lg_pack_split: FP32 volume(s) -> (hi, lo) bf16 [..., channels] with
+    hi + lo = (s x, 0, ..., 0)."""
+    torch = _torch()
+    shape = tuple(x.shape) + (channels,)
+    hi = torch.empty(shape, dtype=torch.bfloat16, device=x.device)
+    lo = torch.empty(shape, dtype=torch.bfloat16, device=x.device)
+    _check("tg_lg_pack_split", load().tg_lg_pack_split(
+        _dptr(x, torch.float32), _dptr(hi, torch.bfloat16), _dptr(lo, torch.bfloat16), x.numel(), int(channels),
+        float(s), _cs(x, stream)))
+    return hi, lo
+
+
+def lg_unpack_f32(t, a, b=None, sa: float = 1.0, sb: float = 1.0, accumulate: bool = False, stream=None):
+    """tg_lg_unpack_f32: a (=|+=) sa t[..., 0]; b = sb t[..., 1] (t FP32)."""
+    torch = _torch()
+    _check("tg_lg_unpack_f32", load().tg_lg_unpack_f32(
+        _dptr(t, torch.float32), int(t.shape[-1]), _dptr(a, torch.float32),
+        None if b is None else _dptr(b, torch.float32), a.numel(), float(sa), float(sb), int(bool(accumulate)),
+        _cs(t, stream)))
+    return a
+
+
+def conv3d_backward_data_split(hi, lo, w, out=None, stream=None):
+    """tg_conv3d_backward_data_split: gy = hi + lo [n, nz, ny, nx, cout] bf16
+    pair -> gx [.., cin] FP32."""
+    torch = _torch()
+    n, nz, ny, nx, cout = hi.shape
+    cin = int(w.shape[2])
+    if lo.shape != hi.shape:
+        raise ValueError("hi and lo must have one shape")
+    if out is None:
+        out = torch.empty((n, nz, ny, nx, cin), dtype=torch.float32, device=hi.device)
+    _check("tg_conv3d_backward_data_split", load().tg_conv3d_backward_data_split(
+        _dptr(hi, torch.bfloat16), _dptr(lo, torch.bfloat16), _dptr(w, torch.float32), _dptr(out, torch.float32), n,
+        nz, ny, nx, cin, cout, _cs(hi, stream)))
+    return out
+
+
+def conv3d_backward_weight_split(x, hi, lo, out=None, stream=None):
+    """tg_conv3d_backward_weight_split: dw [27, cout, cin] FP32 for gy = hi + lo."""
+    torch = _torch()
+    n, nz, ny, nx, cin = x.shape
+    cout = int(hi.shape[4])
+    if lo.shape != hi.shape:
+        raise ValueError("hi and lo must have one shape")
+    if out is None:
+        out = torch.empty((27, cout, cin), dtype=torch.float32, device=x.device)
+    _check("tg_conv3d_backward_weight_split", load().tg_conv3d_backward_weight_split(
+        _dptr(x, torch.bfloat16), _dptr(hi, torch.bfloat16), _dptr(lo, torch.bfloat16), _dptr(out, torch.float32), n,
+        nz, ny, nx, cin, cout, _cs(x, stream)))
+    return out
+
+
+def conv3d_backward_bias_split(hi, lo, out=None, stream=None):
+    """tg_conv3d_backward_bias_split: db [cout] FP32 for gy = hi + lo."""
+    torch = _torch()
+    cout = int(hi.shape[-1])
+    if out is None:
+        out = torch.empty((cout,), dtype=torch.float32, device=hi.device)
+    _check("tg_conv3d_backward_bias_split", load().tg_conv3d_backward_bias_split(
+        _dptr(hi, torch.bfloat16), _dptr(lo, torch.bfloat16), _dptr(out, torch.float32), hi.numel() // cout, cout,
+        _cs(hi, stream)))
+    return out
 
 
 def lg_update(x, net, so: float = 1.0, out=None, stream=None):
