@@ -362,6 +362,7 @@ def run_gpu(args):
     clocks.start()
     time.sleep(0.3)
     n0 = tg.launch_count()
+    tg.kernel_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -369,6 +370,8 @@ def run_gpu(args):
     e1.record(stream)
     e1.synchronize()
     launches = tg.launch_count() - n0
+    kt = tg.kernel_timing_read()
+    tg.kernel_timing(False)
     barrier(world)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
@@ -400,18 +403,16 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     secs_e2e = max_over_ranks(time.perf_counter() - t0, world)
     e2e = replica_value(units_step, args.steps, secs_e2e, world)
+    del bh, xh, xwh, sidh, fdkh
 
-    pk, pk_kind = peaks()
-    # dominant kernel: the matched backprojector (largest share of a step)
-    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 4 * 32 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6   # lane-instructions/s at max clock
-    bp_ops = 32.0 * s_interp    # irreducible lane-ops of the transpose: 32 per sample
-    roof = {"bound": "alu", "achieved": bp_ops / t_bp / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
-            "frac": (bp_ops / t_bp) / alu_peak, "traffic": None,
-            "kernel": "k_bp_matched", "peak_source": f"152 SM x 4 SMSP x 32 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz "
-                                                      f"({pk_kind} max clock)",
-            "ops_per_unit": "32 FP32/INT32 lane-ops per interpolated sample (position, floor, weights, 8 products, 8 adds)"}
-
+    # average launch durations inside the timed region (tg_kernel_timing)
+    avg = {k: (ms * 1e-3 / n if n else None) for k, (ms, n) in kt.items()}
+    t_bp_live = avg["bp_matched"] or t_bp
+    t_fp_live = avg["fp_interp"] or t_fp
+    rates = _probe_rates()
+    roof = roofline_bp(s_interp, t_bp_live, rates)
+    roof_fp = roofline_fp(s_interp, t_fp_live, rates)
+    both = (s_interp / roof_fp["peak_samples_per_s"] + s_interp / roof["peak_samples_per_s"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -420,11 +421,25 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": roof,
+            "roofline_fp": roof_fp,
+            "roofline_fp_bp": {"kernels": "k_fp_interp_tex + k_bp_matched (one A and one A^T)",
+                               "achieved_s": t_fp_live + t_bp_live, "roofline_s": both,
+                               "frac": both / (t_fp_live + t_bp_live)},
+            "kernels_in_timed_region": {k: {"launches": n, "total_ms": ms, "avg_ms": (ms / n if n else None)}
+                                        for k, (ms, n) in kt.items()},
             "kernels_s": {"fp_interp": t_fp, "bp_matched": t_bp, "fp_siddon": t_sid, "bp_fdk": t_bpf,
                           "fdk": t_fdk},
-            "rates": {"fp_interp_samples_per_s": s_interp / t_fp, "bp_matched_pairs_per_s": bp_pairs / t_bp,
+            "rates": {"fp_interp_samples_per_s": s_interp / t_fp_live, "bp_matched_samples_per_s": s_interp / t_bp_live,
+                      "bp_matched_pairs_per_s": bp_pairs / t_bp_live,
                       "fp_siddon_segments_per_s": s_siddon / t_sid, "bp_fdk_pairs_per_s": bp_pairs / t_bpf,
-                      "fp_plus_bp_matched": (s_interp + bp_pairs) / (t_fp + t_bp)}}
+                      "fp_plus_bp_matched": (s_interp + bp_pairs) / (t_fp_live + t_bp_live)},
+            "probe": rates}
+    if rank == 0 and world == 1 and args.learned_pretrain + args.learned_finetune > 0:
+        # the second half of the metric: seconds to PSNR, learned vs CGLS, after
+        # a shortened training pass (its budget is stated in the object)
+        del x, xw, p_sid, v_fdk, b
+        torch.cuda.empty_cache()
+        line["learned"] = learned_measure(args.learned_pretrain, args.learned_finetune, 1, ragged=False)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(g, x_np, b_np)
     if rank == 0:
@@ -432,35 +447,79 @@ def run_gpu(args):
     return 0
 
 
-def run_learned(args):
+def _probe_rates():
+    """Gather and scatter ceilings measured on this device now (libtgprobe)."""
+    from paper_2412_10129_gb300 import probe
+    return {"smem_atomic_conflict_free": probe.smem_atomic(False)["atomics_per_s"],
+            "smem_atomic_random": probe.smem_atomic(True)["atomics_per_s"],
+            "tex_gather_coherent_l1": probe.tex_gather(64, 64, 4, True)["gathers_per_s"],
+            "tex_gather_coherent_l2": probe.tex_gather(512, 512, 64, True)["gathers_per_s"],
+            "l2_sector_gather_gbs": probe.sector_gather(64 << 20)["gbs"]}
+
+
+# DRAM bytes (read + write) of one k_bp_matched launch, from an ncu capture of
+# the kernel as built now (profiles/); None until such a capture exists.
+BP_TRAFFIC_PER_LAUNCH = None
+
+
+def roofline_bp(samples, t, rates):
+    """k_bp_matched: every sample of the interpolated projector scatters eight
+    32-bit fixed-point contributions into shared memory with integer atomic
+    adds, so its ceiling is the SM's shared-memory atomic rate / 8, measured
+    with conflict-free addresses (one 32-lane wavefront per clock)."""
+    peak = rates["smem_atomic_conflict_free"] / 8.0
+    achieved = samples / t
+    return {"bound": "smem_atomic", "kernel": "k_bp_matched", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gsamples/s", "frac": achieved / peak, "traffic": BP_TRAFFIC_PER_LAUNCH,
+            "peak_samples_per_s": peak,
+            "peak_source": "measured conflict-free shared-memory 32-bit atomic adds (libtgprobe tgp_smem_atomic) / "
+                           "8 atomics per sample",
+            "random_scatter_peak": rates["smem_atomic_random"] / 8.0 / 1e9,
+            "unit_of_work": "one trilinear sample of the interpolated projector (8 contributions)"}
+
+
+def roofline_fp(samples, t, rates):
+    """k_fp_interp_tex: every sample gathers its 2x2x2 corners with two
+    2x2 texture gathers; ceiling = the measured warp-coherent tld4 rate (L1-
+    resident array) / 2.  The random-sector L2 ceiling (32 B per sample) is
+    reported beside it: the projector exceeds it because neighbouring
+    samples of a ray reuse L1-resident lines."""
+    peak = rates["tex_gather_coherent_l1"] / 2.0
+    achieved = samples / t
+    return {"bound": "tex_gather", "kernel": "k_fp_interp_tex", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gsamples/s", "frac": achieved / peak, "traffic": None, "peak_samples_per_s": peak,
+            "peak_source": "measured warp-coherent 2x2 FP32 texture gathers, L1-resident array (libtgprobe "
+                           "tgp_tex_gather) / 2 gathers per sample",
+            "l2_random_gather_peak": rates["l2_sector_gather_gbs"] * 1e9 / 32.0 / 1e9}
+
+
+def learned_measure(pretrain, finetune, n_eval, ragged=True, log=None):
     """Seconds to PSNR, learned-gradient scheme vs plain CGLS, on the 256^3
     sparse-view workload (60 angles, 512^2 detector at 0.8 mm, 20-ellipsoid
     phantoms, Poisson noise at I0 = 1e4).  The network is trained here first:
-    pretraining on the same scan at 64^3 (4 mm voxels), then fine-tuning at
-    256^3; held-out phantoms (seeds 5000+) are then reconstructed both ways.
-    The CGLS target is its best PSNR over its iteration count (CGLS
-    semi-converges on noisy data); the learned time is FDK plus the learned
-    steps needed to reach that PSNR.  Timed with synchronisation on both
-    sides (host wall clock over device-resident inputs)."""
+    `pretrain` batches of 2 phantoms on the same scan at 64^3 (4 mm voxels),
+    then `finetune` phantoms at 256^3; `n_eval` held-out phantoms (seeds
+    5000+) are then reconstructed both ways.  The CGLS target is its best
+    PSNR over its iteration count (CGLS semi-converges on noisy data); the
+    learned time is FDK plus the learned steps needed to reach that PSNR.
+    Timed with synchronisation on both sides (host wall clock over
+    device-resident inputs).  Data residuals ||A x - b|| are FP32 projections
+    with FP64 sums."""
     import torch
 
-    from paper_2412_10129_gb300 import build, inputs, learned as L, tg
-    torch.cuda.set_device(0)
-    build.build()
-    tg.load()
-    dev = torch.device("cuda", 0)
+    from paper_2412_10129_gb300 import inputs, learned as L, tg
+    dev = torch.device("cuda", torch.cuda.current_device())
     t_start = time.perf_counter()
     net = L.LearnedGradient(seed=0).to(dev)
     g64, g256 = inputs.config_learned(64), inputs.config_learned(256)
-    l_pre = L.train(net, g64, range(1000, 1000 + 2 * args.pretrain), steps=10, batch=2, lr=3e-4)
-    l_ft = L.train(net, g256, range(3000, 3000 + args.finetune), steps=10, batch=1, lr=1e-4)
+    l_pre = L.train(net, g64, range(1000, 1000 + 2 * pretrain), steps=10, batch=2, lr=3e-4) if pretrain else []
+    l_ft = L.train(net, g256, range(3000, 3000 + finetune), steps=10, batch=1, lr=1e-4) if finetune else []
+    torch.cuda.synchronize()
     t_train = time.perf_counter() - t_start
     eta = 1.0 / L.operator_norm_sq(g256, device=dev)
-    n0 = tg.launch_count()
     rows = []
-    for k in range(args.eval):
+    for k in range(n_eval):
         b, x0, gt = L.make_sample(g256, 5000 + k, device=dev)
-        # CGLS: best PSNR over iterations (coarse grid, then refined)
         cand = {}
         for it in (4, 8, 12, 16, 20, 25, 30, 40):
             cand[it] = L.psnr(tg.cgls(g256, b, it), gt)
@@ -471,7 +530,6 @@ def run_learned(args):
         k_best = max(cand, key=cand.get)
         p_cgls = cand[k_best]
         t_cgls = L.timed(lambda: tg.cgls(g256, b, k_best))
-        # learned: PSNR after every step, then the time to reach the CGLS PSNR
         with torch.no_grad():
             x = tg.fdk(g256, b)
             curve = []
@@ -491,47 +549,60 @@ def run_learned(args):
         t_reach = L.timed(lambda: recon(reach)) if reach else None
         x_l = recon(10)
         x_c = tg.cgls(g256, b, k_best)
-        # data residual ||A x - b|| with FP64 accumulation (interpolated projector)
         res = {name: float(torch.linalg.vector_norm((tg.forward(g256, v) - b).double()))
                for name, v in (("learned", x_l), ("cgls", x_c), ("fdk", x0))}
         rows.append({"seed": 5000 + k, "cgls_psnr": p_cgls, "cgls_iters": k_best, "cgls_s": t_cgls,
                      "learned_psnr_10": curve[-1], "learned_psnr_curve": curve, "learned_steps_to_cgls_psnr": reach,
                      "learned_s_to_cgls_psnr": t_reach, "learned_s_10": t_full, "fdk_psnr": L.psnr(x0, gt),
-                     "residual": res})
-    # batched inference over 8 uneven volumes (192^3 - 320^3 at 1 mm): each
-    # convolution covers all volumes in one launch
-    sizes = (192, 208, 224, 240, 256, 272, 288, 320)
-    geos = [inputs.circular_geometry((n,) * 3, (1.0,) * 3, (2 * n, 2 * n), (0.8, 0.8), 60, 1000.0, 1536.0)
-            for n in sizes]
-    data = [L.make_sample(gg, 7000 + i, device=dev) for i, gg in enumerate(geos)]
-    etas = [1.0 / L.operator_norm_sq(gg, device=dev) for gg in geos]
-    bs, x0s = [d[0] for d in data], [d[1] for d in data]
-    t_rag = L.timed(lambda: L.infer_ragged(net, geos, bs, x0s, steps=10, etas=etas), reps=2)
-
-    def one_by_one():
-        with torch.no_grad():
-            for gg, bb, xx, ee in zip(geos, bs, x0s, etas):
-                net(xx, bb, gg, steps=10, eta=ee)
-
-    t_seq = L.timed(one_by_one, reps=2)
-    xs = L.infer_ragged(net, geos, bs, x0s, steps=10, etas=etas)
-    ragged = {"sizes": list(sizes), "voxels": int(sum(n ** 3 for n in sizes)), "steps": 10,
-              "seconds_batched": t_rag, "seconds_one_by_one": t_seq,
-              "voxel_steps_per_s": 10 * sum(n ** 3 for n in sizes) / t_rag,
-              "psnr": [L.psnr(x, d[2]) for x, d in zip(xs, data)],
-              "fdk_psnr": [L.psnr(d[1], d[2]) for d in data]}
-    del data, bs, x0s, xs
-    torch.cuda.empty_cache()
+                     "residual_fp64_sum": res})
+    out = {"workload": "256^3 at 1 mm, 60 angles over 2pi, 512x512 detector at 0.8 mm, 20-ellipsoid phantoms, "
+                       "Poisson noise I0=1e4; learned gradient 10 steps, 5x conv3d 3^3 32 ch (BF16, FP32 acc)",
+           "training": {"pretrain_64_batches_of_2": pretrain, "finetune_256_phantoms": finetune,
+                        "seconds": t_train, "loss_first": l_pre[:3], "loss_last": (l_ft or l_pre)[-3:]},
+           "per_phantom": rows}
     reached = [r["learned_s_to_cgls_psnr"] for r in rows if r["learned_s_to_cgls_psnr"] is not None]
-    line = {"metric": "seconds to PSNR: learned vs CGLS", "value": float(np.mean(reached)) if len(reached) == len(rows)
-            else None, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "bf16/f32",
-            "data": "synthetic", "cgls_value": float(np.mean([r["cgls_s"] for r in rows])),
-            "config": {"workload": "256^3 at 1 mm, 60 angles over 2pi, 512x512 detector at 0.8 mm, 20-ellipsoid "
-                                   "phantoms, Poisson noise I0=1e4; learned gradient 10 steps, 5x conv3d 3^3 32 ch",
-                       "training": {"pretrain_64_batches": args.pretrain, "finetune_256_phantoms": args.finetune,
-                                    "seconds": t_train, "loss_first": l_pre[:3], "loss_last": l_ft[-3:]}},
-            "gpu_launches_eval": tg.launch_count() - n0,
-            "per_phantom": rows, "ragged_inference": ragged}
+    out["learned_s_to_cgls_psnr"] = float(np.mean(reached)) if rows and len(reached) == len(rows) else None
+    out["cgls_s_to_best_psnr"] = float(np.mean([r["cgls_s"] for r in rows])) if rows else None
+    if ragged:
+        sizes = (192, 208, 224, 240, 256, 272, 288, 320)
+        geos = [inputs.circular_geometry((n,) * 3, (1.0,) * 3, (2 * n, 2 * n), (0.8, 0.8), 60, 1000.0, 1536.0)
+                for n in sizes]
+        data = [L.make_sample(gg, 7000 + i, device=dev) for i, gg in enumerate(geos)]
+        etas = [1.0 / L.operator_norm_sq(gg, device=dev) for gg in geos]
+        bs, x0s = [d[0] for d in data], [d[1] for d in data]
+        t_rag = L.timed(lambda: L.infer_ragged(net, geos, bs, x0s, steps=10, etas=etas), reps=2)
+
+        def one_by_one():
+            with torch.no_grad():
+                for gg, bb, xx, ee in zip(geos, bs, x0s, etas):
+                    net(xx, bb, gg, steps=10, eta=ee)
+
+        t_seq = L.timed(one_by_one, reps=2)
+        xs = L.infer_ragged(net, geos, bs, x0s, steps=10, etas=etas)
+        out["ragged_inference"] = {"sizes": list(sizes), "voxels": int(sum(n ** 3 for n in sizes)), "steps": 10,
+                                   "seconds_batched": t_rag, "seconds_one_by_one": t_seq,
+                                   "voxel_steps_per_s": 10 * sum(n ** 3 for n in sizes) / t_rag,
+                                   "psnr": [L.psnr(x, d[2]) for x, d in zip(xs, data)],
+                                   "fdk_psnr": [L.psnr(d[1], d[2]) for d in data]}
+        del data, bs, x0s, xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_learned(args):
+    """The learned-vs-CGLS measurement on its own (one JSON line)."""
+    import torch
+
+    from paper_2412_10129_gb300 import build, tg
+    torch.cuda.set_device(0)
+    build.build()
+    tg.load()
+    n0 = tg.launch_count()
+    res = learned_measure(args.pretrain, args.finetune, args.eval, ragged=True)
+    line = {"metric": "seconds to PSNR: learned vs CGLS", "value": res["learned_s_to_cgls_psnr"], "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "bf16/f32", "data": "synthetic",
+            "cgls_value": res["cgls_s_to_best_psnr"], "config": {"workload": res["workload"]},
+            "gpu_launches": tg.launch_count() - n0, "learned": res}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -615,6 +686,76 @@ def run_solvers(args):
     return 0
 
 
+def run_micro(args):
+    """The micro-CT workload on its own (one JSON line): 1024^3 at 0.125 mm,
+    1600 angles over 2 pi, 1024^2 detector at 0.2 mm, every angle with its
+    own seeded detector offset, in-plane tilt and source jitter; phantom =
+    200 ellipsoids + a porous cylinder, data = its Siddon projection with
+    Poisson noise at I0 = 1e5.  Forward and back projection throughput (one
+    launch each after a warm-up one, CUDA events) and 10 CGLS iterations."""
+    import torch
+
+    from paper_2412_10129_gb300 import build, inputs, tg
+    torch.cuda.set_device(0)
+    build.build()
+    tg.load()
+    dev = torch.device("cuda", 0)
+    g = inputs.config_micro()
+    x_np = inputs.micro_phantom(g, seed=1)
+    x = torch.from_numpy(x_np).to(dev)
+    b = inputs.poisson_noise_device(tg.forward(g, x, "siddon"), 1e5, seed=2)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, warm=True):
+        if warm:
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    s_interp = tg.count_samples(g, "interp")
+    s_siddon = tg.count_samples(g, "siddon")
+    pairs = int(np.prod(g.vol_shape)) * g.nAngles
+    p_tmp = torch.empty(g.proj_shape, device=dev)
+    v_tmp = torch.empty(g.vol_shape, device=dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t = {"fp_interp": timed(lambda: tg.forward(g, x, "interp", out=p_tmp)),
+         "fp_siddon": timed(lambda: tg.forward(g, x, "siddon", out=p_tmp)),
+         "bp_matched": timed(lambda: tg.backproject(g, b, "matched", out=v_tmp)),
+         "bp_fdk": timed(lambda: tg.backproject(g, b, "fdk", out=v_tmp))}
+    del p_tmp, v_tmp
+    torch.cuda.empty_cache()
+    hist = []
+    t["cgls_10"] = timed(lambda: hist.append(tg.cgls(g, b, 10, resid=True)[1]), warm=False)
+    clk = clocks.stop()
+    rates = _probe_rates()
+    value = (s_interp + pairs) / (t["fp_interp"] + t["bp_matched"])
+    line = {"metric": "FP+BP voxel-samples/s at 1024^3 micro-CT (per-angle jitter)", "value": value, "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1024^3 FP32 volume (0.125 mm), 1600 angles over 2pi, 1024x1024 detector (0.2 mm), "
+                                   "per-angle detector offset +-2 px, tilt +-0.5 deg, source jitter +-0.5 mm; "
+                                   "200 ellipsoids + porous cylinder; Poisson noise I0=1e5"},
+            "seconds": t, "clocks": clk,
+            "units": {"interp_samples": s_interp, "siddon_segments": s_siddon, "voxel_angle_pairs": pairs},
+            "rates": {"fp_interp_samples_per_s": s_interp / t["fp_interp"],
+                      "fp_siddon_segments_per_s": s_siddon / t["fp_siddon"],
+                      "bp_matched_samples_per_s": s_interp / t["bp_matched"],
+                      "bp_fdk_pairs_per_s": pairs / t["bp_fdk"],
+                      "cgls_s_per_iteration": t["cgls_10"] / 10},
+            "cgls_residual_history": [float(v) for v in np.asarray(hist[-1]).ravel()],
+            "roofline": roofline_bp(s_interp, t["bp_matched"], rates),
+            "roofline_fp": roofline_fp(s_interp, t["fp_interp"], rates)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(g, x_np, b.cpu().numpy())
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _siddon_gpu(g, x_np, dev):
     import torch
 
@@ -629,16 +770,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tg", choices=["tg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="clinical", choices=sorted(CASES) + ["learned", "solvers"],
+    ap.add_argument("--case", default="clinical", choices=sorted(CASES) + ["learned", "solvers", "micro"],
                     help="workload; 'medium' is the half-resolution scan used for profiler captures; 'learned' "
                          "trains the learned-gradient scheme and times it against CGLS; 'solvers' times one "
                          "iteration of every solver and the extra operators at 512^3")
     ap.add_argument("--pretrain", type=int, default=300, help="learned: 64^3 training batches (2 phantoms each)")
     ap.add_argument("--finetune", type=int, default=40, help="learned: 256^3 training phantoms")
     ap.add_argument("--eval", type=int, default=2, help="learned: held-out phantoms")
+    ap.add_argument("--learned-pretrain", type=int, default=150,
+                    help="default case: 64^3 training batches of the learned-vs-CGLS object (0 = leave it out)")
+    ap.add_argument("--learned-finetune", type=int, default=20,
+                    help="default case: 256^3 training phantoms of the learned-vs-CGLS object")
     args = ap.parse_args()
     if args.case == "learned":
         return run_learned(args) if args.impl != "reference" else 0
+    if args.case == "micro":
+        return run_micro(args) if args.impl != "reference" else 0
     if args.case == "solvers":
         args.case = "clinical"
         return run_solvers(args) if args.impl != "reference" else 0

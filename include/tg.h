@@ -133,7 +133,10 @@ tg_status tg_forward(const tg_geometry *geo, const double *angles, int nAngles, 
                      float *proj, int method, int batch, void *stream);
 
 /* Backprojection (A^T of Eq. 4 for TG_MATCHED, the FDK backprojection for
- * TG_FDK_WEIGHT).  vol is overwritten. */
+ * TG_FDK_WEIGHT).  vol is overwritten.  TG_MATCHED accumulates in fixed
+ * point scaled by max |proj| of each batch item; when that item's
+ * projections hold an Inf or a NaN, every voxel of its volume is NaN (the
+ * solvers built on it then return NaN instead of finite-looking values). */
 tg_status tg_backproject(const tg_geometry *geo, const double *angles, int nAngles,
                          const float *proj, float *vol, int method, int batch, void *stream);
 

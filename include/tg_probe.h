@@ -44,6 +44,12 @@ int tgp_tex_gather(int nx, int ny, int nlayers, int coherent, int reps, double *
  * lane hits a random word.  *atomics_per_s: lane atomics per second. */
 int tgp_smem_atomic(int random, int reps, double *atomics_per_s, double *ms_per_launch);
 
+/* tgp_smem_atomic for another word type: kind 0 = 32-bit unsigned (the same
+ * as tgp_smem_atomic), 1 = 64-bit unsigned on 8192 words, 2 = FP32 on
+ * 16384 words; kind 3 replaces the atomics by plain FP32 loads (the
+ * shared-memory gather a trilinear sample would need). */
+int tgp_smem_atomic_kind(int kind, int random, int reps, double *atomics_per_s, double *ms_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

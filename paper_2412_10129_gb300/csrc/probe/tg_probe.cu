@@ -118,6 +118,40 @@ __global__ void __launch_bounds__(1024) k_smem_atomic(int trips, unsigned *sink)
     if (sm[threadIdx.x] == 0xFFFFFFFFu) sink[0] = 1u;  // keeps the atomics (never true)
 }
 
+// The same pattern on 8192 64-bit words (KIND 1: unsigned long long adds),
+// 16384 FP32 words (KIND 2: float adds) or plain FP32 loads (KIND 3).
+template <bool RANDOM, int KIND>
+__global__ void __launch_bounds__(1024) k_smem_atomic_kind(int trips, unsigned *sink) {
+    constexpr unsigned WORDS = KIND == 1 ? 8192 : 16384;
+    extern __shared__ unsigned long long sm64[];
+    unsigned long long *w64 = sm64;
+    float *wf = reinterpret_cast<float *>(sm64);
+    for (unsigned i = threadIdx.x; i < 8192u; i += blockDim.x) sm64[i] = 0ull;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned s = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 0x9e3779b9u;
+    if (s == 0) s = 1;
+    unsigned off[8];
+    float lsum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) off[j] = RANDOM ? xorshift(s) : (lane + 32u * (unsigned)(j * 61 + threadIdx.x / 32));
+    for (int t = 0; t < trips; ++t) {
+        const unsigned sh = RANDOM ? xorshift(s) : 32u * (unsigned)(t * 7);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned a = (off[j] + sh) & (WORDS - 1u);
+            if (KIND == 1)
+                atomicAdd(&w64[a], 1ull);
+            else if (KIND == 2)
+                atomicAdd(&wf[a], 1.f);
+            else
+                lsum += wf[a];
+        }
+    }
+    __syncthreads();
+    if (sm64[threadIdx.x] == ~0ull || lsum == 1.2345e-30f) sink[0] = 1u;  // keeps the accesses (never true)
+}
+
 struct Timer {
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -216,6 +250,52 @@ int tgp_smem_atomic(int random, int reps, double *atomics_per_s, double *ms_per_
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.e0, t.e1);
     if (e == cudaSuccess) {
         const double n = (double)blocks * threads * trips * 8.0 * reps;  // lane atomics
+        *atomics_per_s = n / (ms * 1e-3);
+        if (ms_per_launch) *ms_per_launch = ms / reps;
+    }
+    if (sink) cudaFree(sink);
+    return (int)e;
+}
+
+int tgp_smem_atomic_kind(int kind, int random, int reps, double *atomics_per_s, double *ms_per_launch) {
+    if (!atomics_per_s || reps <= 0 || kind < 0 || kind > 3) return (int)cudaErrorInvalidValue;
+    if (kind == 0) return tgp_smem_atomic(random, reps, atomics_per_s, ms_per_launch);
+    Timer t;
+    cudaError_t e = t.init();
+    unsigned *sink = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(unsigned));
+    const int threads = 1024, smem = 65536, trips = 512;
+    const void *fn = kind == 1 ? (random ? (const void *)k_smem_atomic_kind<true, 1> : (const void *)k_smem_atomic_kind<false, 1>)
+                     : kind == 2 ? (random ? (const void *)k_smem_atomic_kind<true, 2> : (const void *)k_smem_atomic_kind<false, 2>)
+                                 : (random ? (const void *)k_smem_atomic_kind<true, 3> : (const void *)k_smem_atomic_kind<false, 3>);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+    const int blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    auto launch = [&]() {
+        if (kind == 1) {
+            if (random) k_smem_atomic_kind<true, 1><<<blocks, threads, smem, t.s>>>(trips, sink);
+            else k_smem_atomic_kind<false, 1><<<blocks, threads, smem, t.s>>>(trips, sink);
+        } else if (kind == 2) {
+            if (random) k_smem_atomic_kind<true, 2><<<blocks, threads, smem, t.s>>>(trips, sink);
+            else k_smem_atomic_kind<false, 2><<<blocks, threads, smem, t.s>>>(trips, sink);
+        } else {
+            if (random) k_smem_atomic_kind<true, 3><<<blocks, threads, smem, t.s>>>(trips, sink);
+            else k_smem_atomic_kind<false, 3><<<blocks, threads, smem, t.s>>>(trips, sink);
+        }
+        return cudaGetLastError();
+    };
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(t.e0, t.s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(t.e1, t.s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t.e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.e0, t.e1);
+    if (e == cudaSuccess) {
+        const double n = (double)blocks * threads * trips * 8.0 * reps;
         *atomics_per_s = n / (ms * 1e-3);
         if (ms_per_launch) *ms_per_launch = ms / reps;
     }

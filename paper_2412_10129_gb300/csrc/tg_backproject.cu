@@ -100,15 +100,18 @@ __global__ void __launch_bounds__(256) k_bp_apply(const float *__restrict__ acc,
 }
 
 // max |y| per batch item (blockIdx.y), as the bit pattern of a non-negative
-// float (ordered like an unsigned int)
+// float (ordered like an unsigned int).  The maximum is taken over the bit
+// patterns, so an Inf (0x7f800000) or a NaN (above it) is never lost: the
+// matched backprojector reads a non-finite maximum as "the data hold Inf or
+// NaN" and returns NaN.
 __global__ void k_absmax(const float *__restrict__ y, size_t n, unsigned int *out) {
     const float *yb = y + (size_t)blockIdx.y * n;
-    float m = 0.f;
+    unsigned int m = 0u;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(yb[i]));
+        m = max(m, __float_as_uint(yb[i]) & 0x7fffffffu);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, __float_as_uint(m));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, m);
 }
 
 // ---- matched transpose ------------------------------------------------------
@@ -236,6 +239,33 @@ __device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float 
     }
 }
 
+// 64-bit fixed point: each contribution is its FP32 product (ys already
+// carries the power-of-two scale) rounded to an integer, added with a 64-bit
+// integer atomic; the sums are exact and order-independent, and a product
+// keeps FP32 relative precision down to 2^-62 of the scale's range.
+__device__ __forceinline__ void scatter_sample64(unsigned long long *accc, int k, float gx, float gy, float gz,
+                                                 float sx, float sy, float sz, float ys, int ox, int oy, int oz) {
+    const float kf = (float)k;
+    const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
+    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
+    const int lx = min(max((int)fx - ox, 0), RX - 2);
+    const int ly = min(max((int)fy - oy, 0), RY - 2);
+    const int lz = min(max((int)fz - oz, 0), RZ - 2);
+    const float wx = x - fx, wy = yy - fy, wz = z - fz;
+    const float c0 = ys * (1.f - wz), c1 = ys * wz;
+    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
+    const float ux = 1.f - wx;
+    unsigned long long *c = accc + lz * PP + ly * PX + lx;
+    atomicAdd(c, (unsigned long long)__float2ll_rn(b00 * ux));
+    atomicAdd(c + 1, (unsigned long long)__float2ll_rn(b00 * wx));
+    atomicAdd(c + PX, (unsigned long long)__float2ll_rn(b01 * ux));
+    atomicAdd(c + PX + 1, (unsigned long long)__float2ll_rn(b01 * wx));
+    atomicAdd(c + PP, (unsigned long long)__float2ll_rn(b10 * ux));
+    atomicAdd(c + PP + 1, (unsigned long long)__float2ll_rn(b10 * wx));
+    atomicAdd(c + PP + PX, (unsigned long long)__float2ll_rn(b11 * ux));
+    atomicAdd(c + PP + PX + 1, (unsigned long long)__float2ll_rn(b11 * wx));
+}
+
 // F32: accumulate with FP32 shared atomics instead (read-modify-write loops,
 // ~2x slower here; the sums then depend on the order of the atomics at the
 // 1e-7 level).  Chosen where each voxel's sum must keep its own relative
@@ -245,7 +275,7 @@ __device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float 
 // One brick (bx, by, bz) of one volume: pb are the volume's projections,
 // vb its output (and the SIRT weight's) voxels, gmax its max |y|; the
 // epilogue writes vb directly and adds the FP64 norm to ep.norm[0].
-template <int MODE, bool F32, bool PAR>
+template <int MODE, bool F32, bool PAR, bool I64 = false>
 __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, float *__restrict__ vb,
                                                  const Angle *__restrict__ angles, const Grid &g, const BpEpilogue &ep,
                                                  float gmax, int bx, int by, int bz) {
@@ -264,10 +294,16 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     RayRec *rays = reinterpret_cast<RayRec *>(acc + 2 * ACC_WORDS);
     __shared__ int s_cnt[2];  // rays listed, rays handed out
     const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
-    const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
+    float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
+    if (I64 && scale > 0.f) {
+        // 2^E with gmax 2^E wbound FLUSH <= 2^62: one flush period's sums fit 63 bits
+        const float e = floorf(62.f - log2f(gmax) - log2f(g.wbound * (float)FLUSH));
+        scale = exp2f(fminf(fmaxf(e, -120.f), 120.f));
+    }
     const float inv_scale = scale > 0.f ? 1.f / scale : 0.f;
     const float scale_f = FINE * scale, inv_scale_f = inv_scale * (1.f / FINE);
-    const float ybig = gmax * (1.f / FINE);
+    const float ybig = I64 ? -1.f : gmax * (1.f / FINE);  // 64-bit: one class (every ray "big")
+    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
     // owned voxel j of this thread: (lane, warp + 16 (j & 1), j >> 1)
     const int obase = RIM * PP + (warp + RIM) * PX + lane + RIM;
     const int ox = x0 - RIM, oy = y0 - RIM, oz = z0 - RIM;  // voxel of accumulator cell (0, 0, 0)
@@ -276,7 +312,9 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     for (int j = 0; j < OWN; ++j) own[j] = 0.f;
     for (int i = tid; i < 2 * ACC_WORDS; i += MT) acc[i] = 0u;
     __syncthreads();
-    for (int a0 = 0; a0 < g.nA; a0 += FLUSH) {
+    // Inf or NaN in the data: no fixed-point scale exists; every voxel is NaN
+    const bool nonfinite = !F32 && !(gmax <= 3.4028235e38f);  // (fixed point, 32- or 64-bit)
+    for (int a0 = 0; a0 < (nonfinite ? 0 : g.nA); a0 += FLUSH) {
         const int a1 = min(a0 + FLUSH, g.nA);
         for (int a = a0; a < a1; ++a) {
             const Angle &A = angles[a];
@@ -381,8 +419,14 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
                     // two samples per trip (the second adds zeros past the ray's end)
-                    scatter_sample<F32>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
-                    scatter_sample<F32>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
+                    if (I64) {
+                        scatter_sample64(acc64, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
+                        scatter_sample64(acc64, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
+                    } else {
+                        scatter_sample<F32>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
+                        scatter_sample<F32>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy,
+                                            oz);
+                    }
                     k += 2;
                 }
                 __syncthreads();  // the list is refilled by the next chunk
@@ -393,7 +437,10 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
 #pragma unroll
         for (int j = 0; j < OWN; ++j) {
             const int o = obase + (j >> 1) * PP + (j & 1) * 16 * PX;
-            if (F32) {
+            if (I64) {
+                own[j] = fmaf(__ll2float_rn((long long)acc64[o]), inv_scale, own[j]);
+                acc64[o] = 0ull;
+            } else if (F32) {
                 float *af = reinterpret_cast<float *>(acc);
                 own[j] += af[o];
                 af[o] = 0.f;
@@ -408,6 +455,10 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
         __syncthreads();
     }
     // owned voxels to the output
+    if (nonfinite) {
+#pragma unroll
+        for (int j = 0; j < OWN; ++j) own[j] = __int_as_float(0x7fc00000);
+    }
     double part = 0.0;
 #pragma unroll
     for (int j = 0; j < OWN; ++j) {
@@ -425,6 +476,39 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
         }
     }
     if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
+}
+
+// The same contributions as scatter_sample (bit for bit): the sample index
+// arrives as an exact float, and the integral float floor(x) becomes an int
+// through the 1.5 * 2^23 addend (exact for |x| < 2^22) instead of a
+// float-to-int conversion; mo* = MAGIC_BITS + o*.
+__device__ __forceinline__ void scatter_sample_fx(unsigned int *accc, float kf, float gx, float gy, float gz,
+                                                  float sx, float sy, float sz, float ys, int mox, int moy,
+                                                  int moz) {
+    const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
+    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
+    const int lx = min(max(__float_as_int(fx + MAGIC) - mox, 0), RX - 2);
+    const int ly = min(max(__float_as_int(fy + MAGIC) - moy, 0), RY - 2);
+    const int lz = min(max(__float_as_int(fz + MAGIC) - moz, 0), RZ - 2);
+    const float wx = x - fx, wy = yy - fy, wz = z - fz;
+    const float c0 = ys * (1.f - wz), c1 = ys * wz;
+    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
+    const float ux = 1.f - wx;
+    unsigned int *c = accc + lz * PP + ly * PX + lx;
+    atomicAdd(c, fixq(b00, ux));
+    atomicAdd(c + 1, fixq(b00, wx));
+    atomicAdd(c + PX, fixq(b01, ux));
+    atomicAdd(c + PX + 1, fixq(b01, wx));
+    atomicAdd(c + PP, fixq(b10, ux));
+    atomicAdd(c + PP + 1, fixq(b10, wx));
+    atomicAdd(c + PP + PX, fixq(b11, ux));
+    atomicAdd(c + PP + PX + 1, fixq(b11, wx));
+}
+
+template <bool PAR>
+__device__ __noinline__ void ray_frame_outlined(const Angle *A, const Grid *g, int iu, int iv, Ray *r) {
+    float Ld;
+    ray_frame<PAR>(*A, *g, iu, iv, *r, Ld);
 }
 
 // ---- compact-record variant ---------------------------------------------
@@ -488,7 +572,7 @@ __device__ __forceinline__ bool region_ray8(const Angle &A, const Grid &g, float
     return true;
 }
 
-template <int MODE, bool PAR, int NT, bool OG, bool LF>
+template <int MODE, bool PAR, int NT, bool OG, bool LF, bool FX>
 __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, float *__restrict__ vb,
                                                   const Angle *__restrict__ angles, const Grid &g,
                                                   const BpEpilogue &ep, float gmax, int bx, int by, int bz) {
@@ -513,16 +597,23 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
     const float ybig = gmax * (1.f / FINE);
     const int obase = RIM * PP + (warp + RIM) * PX + lane + RIM;
     const int ox = x0 - RIM, oy = y0 - RIM, oz = z0 - RIM;
+    const int mox = MAGIC_BITS + ox, moy = MAGIC_BITS + oy, moz = MAGIC_BITS + oz;
     float own[OG ? 1 : OWNN];
 #pragma unroll
     for (int j = 0; j < (OG ? 1 : OWNN); ++j) own[j] = 0.f;
     for (int i = tid; i < 2 * ACC_WORDS; i += NT) acc[i] = 0u;
     __syncthreads();
+    const bool nonfinite = !(gmax <= 3.4028235e38f);  // Inf or NaN in the data: every voxel is NaN
     bool first = true;
-    for (int a0 = 0; a0 < g.nA; a0 += FLUSH) {
+    __shared__ Angle sA;  // the current angle's constants (read by every lane from shared memory)
+    for (int a0 = 0; a0 < (nonfinite ? 0 : g.nA); a0 += FLUSH) {
         const int a1 = min(a0 + FLUSH, g.nA);
         for (int a = a0; a < a1; ++a) {
-            const Angle &A = angles[a];
+            __syncthreads();  // every thread is done with the previous angle's constants
+            if (tid < (int)(sizeof(Angle) / sizeof(float4)))
+                reinterpret_cast<float4 *>(&sA)[tid] = __ldg(reinterpret_cast<const float4 *>(angles + a) + tid);
+            __syncthreads();
+            const Angle &A = sA;
             float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -610,8 +701,12 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
                                 const RayRec8 rr = rays[idx < nl ? idx : RAYCAP8 - 1 - (idx - nl)];
                                 const int iu = (int)(rr.iuv & 0xffffu), iv = (int)(rr.iuv >> 16);
                                 Ray q;
-                                float Ld;
-                                ray_frame<PAR>(A, g, iu, iv, q, Ld);
+                                if (FX) {
+                                    ray_frame_outlined<PAR>(&A, &g, iu, iv, &q);
+                                } else {
+                                    float Ld;
+                                    ray_frame<PAR>(A, g, iu, iv, q, Ld);
+                                }
                                 gx = q.gx;
                                 gy = q.gy;
                                 gz = q.gz;
@@ -631,8 +726,16 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
                     }
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
-                    scatter_sample<false>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
-                    scatter_sample<false>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
+                    if (FX) {
+                        const float kf = (float)k;
+                        scatter_sample_fx(accc, kf, gx, gy, gz, sx, sy, sz, ys, mox, moy, moz);
+                        scatter_sample_fx(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, mox, moy,
+                                          moz);
+                    } else {
+                        scatter_sample<false>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
+                        scatter_sample<false>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy,
+                                              oz);
+                    }
                     k += 2;
                 }
                 __syncthreads();
@@ -665,7 +768,8 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
         const int ix = x0 + lane, iy = y0 + warp + NW * (j % YR), iz = z0 + j / YR;
         const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
         const size_t widx = ok ? ((size_t)iz * g.ny + iy) * g.nx + ix : 0;
-        const float sum = OG ? (ok ? (first ? 0.f : vb[widx]) : 0.f) : own[OG ? 0 : j];
+        float sum = OG ? (ok ? (first ? 0.f : vb[widx]) : 0.f) : own[OG ? 0 : j];
+        if (nonfinite) sum = __int_as_float(0x7fc00000);
         if (MODE == BP_STORE_NORM) {
             const float v = ep.scale * sum;
             if (ok) {
@@ -679,7 +783,7 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
     if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
 }
 
-template <int MODE, bool PAR, int NT, bool OG, bool LF>
+template <int MODE, bool PAR, int NT, bool OG, bool LF, bool FX>
 __global__ void __launch_bounds__(NT, 1)
     k_bp_matched8(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
                   BpEpilogue ep, int nbx, int nby) {
@@ -687,12 +791,12 @@ __global__ void __launch_bounds__(NT, 1)
     BpEpilogue e = ep;
     if (e.norm) e.norm += b;
     const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-    bp_matched_brick8<MODE, PAR, NT, OG, LF>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
+    bp_matched_brick8<MODE, PAR, NT, OG, LF, FX>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
                                              __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby,
                                              bl / (nbx * nby));
 }
 
-template <int MODE, bool F32, bool PAR>
+template <int MODE, bool F32, bool PAR, bool I64 = false>
 __global__ void __launch_bounds__(MT, 1)
     k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
                  BpEpilogue ep, int nbx, int nby) {
@@ -700,8 +804,9 @@ __global__ void __launch_bounds__(MT, 1)
     BpEpilogue e = ep;
     if (e.norm) e.norm += b;
     const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-    bp_matched_brick<MODE, F32, PAR>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
-                                __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
+    bp_matched_brick<MODE, F32, PAR, I64>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
+                                          __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby,
+                                          bl / (nbx * nby));
 }
 
 // Volumes of different sizes and geometries in one launch (packed back to
@@ -744,13 +849,13 @@ struct AbsRagged {
 __global__ void k_absmax_ragged(const float *__restrict__ y, const __grid_constant__ AbsRagged t, unsigned int *out) {
     const int v = blockIdx.y;
     const float *yv = y + t.p0[v];
-    float m = 0.f;
+    unsigned int m = 0u;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < t.n[v];
          i += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(yv[i]));
+        m = max(m, __float_as_uint(yv[i]) & 0x7fffffffu);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + v, __float_as_uint(m));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + v, m);
 }
 
 // FDK-weighted backprojection; each thread owns a column of ZC voxels.
@@ -813,20 +918,28 @@ __global__ void __launch_bounds__(256) k_bp_fdk(const float *__restrict__ proj, 
     }
 }
 
-template <int MODE, bool F32, bool PAR>
+template <int MODE, bool F32, bool PAR, bool I64 = false>
 cudaError_t launch_matched_t(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
                              const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_bp_matched<MODE, F32, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         MATCHED_SMEM);
+    auto kern = k_bp_matched<MODE, F32, PAR, I64>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MATCHED_SMEM);
     if (e != cudaSuccess) return e;
-    k_bp_matched<MODE, F32, PAR><<<grid, MT, MATCHED_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
+    kern<<<grid, MT, MATCHED_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
     return cudaSuccess;
 }
 
-template <int MODE, int NT, bool OG, bool LF>
+// 64-bit fixed point in place of FP32 accumulation (experiment switch TG_BP_I64)
+template <int MODE>
+cudaError_t launch_matched_i64(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
+                               const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
+    return g.parallel ? launch_matched_t<MODE, false, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                      : launch_matched_t<MODE, false, false, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+}
+
+template <int MODE, int NT, bool OG, bool LF, bool FX = false>
 cudaError_t launch_matched8_t(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
                               const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    auto kern = k_bp_matched8<MODE, false, NT, OG, LF>;
+    auto kern = k_bp_matched8<MODE, false, NT, OG, LF, FX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MATCHED8_SMEM);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, MATCHED8_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
@@ -852,6 +965,9 @@ cudaError_t launch_matched8(dim3 grid, const float *proj, float *vol, const Angl
     if (v == "g512lf") return launch_matched8_t<MODE, 512, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
     if (v == "g1024") return launch_matched8_t<MODE, 1024, true, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
     if (v == "g1024lf") return launch_matched8_t<MODE, 1024, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "x512lf") return launch_matched8_t<MODE, 512, false, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "x1024lf") return launch_matched8_t<MODE, 1024, false, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+    if (v == "xg1024lf") return launch_matched8_t<MODE, 1024, true, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
     return cudaErrorNotSupported;
 }
 
@@ -883,6 +999,14 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
         dim3 grid((unsigned)(nbx * nby * nbz), batch);
         const bool f32 = ep.fp32_acc != 0;
         KernelTimer kt(TG_KT_BP_MATCHED, s);
+        if (f32 && getenv("TG_BP_I64") && (mode == BP_STORE || mode == BP_SIRT || mode == BP_MLEM)) {
+            e = mode == BP_STORE ? launch_matched_i64<BP_STORE>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                : mode == BP_SIRT ? launch_matched_i64<BP_SIRT>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
+                                  : launch_matched_i64<BP_MLEM>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+            if (e != cudaSuccess) return e;
+            count_launch();
+            return cudaGetLastError();
+        }
         if (mode == BP_STORE || mode == BP_STORE_NORM) {
             e = mode == BP_STORE ? launch_matched8<BP_STORE>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
                                  : launch_matched8<BP_STORE_NORM>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);

@@ -23,6 +23,7 @@ def load():
         lib.tgp_sector_gather.argtypes = [ctypes.c_size_t, ctypes.c_int, D, D]
         lib.tgp_tex_gather.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
         lib.tgp_smem_atomic.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
+        lib.tgp_smem_atomic_kind.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
         _lib = lib
     return _lib
 
@@ -48,13 +49,14 @@ def tex_gather(nx: int, ny: int, nlayers: int, coherent: bool, reps: int = 10) -
             "coherent": bool(coherent), "gathers_per_s": rate.value, "ms_per_launch": ms.value}
 
 
-def smem_atomic(random: bool, reps: int = 10) -> dict:
-    """32-bit shared-memory integer atomics: conflict-free or random words."""
+def smem_atomic(random: bool, reps: int = 10, kind: str = "u32") -> dict:
+    """Shared-memory atomic adds (u32, u64 or f32 words): conflict-free or random words."""
     rate, ms = ctypes.c_double(), ctypes.c_double()
-    rc = load().tgp_smem_atomic(1 if random else 0, int(reps), ctypes.byref(rate), ctypes.byref(ms))
+    k = {"u32": 0, "u64": 1, "f32": 2, "load": 3}[kind]
+    rc = load().tgp_smem_atomic_kind(k, 1 if random else 0, int(reps), ctypes.byref(rate), ctypes.byref(ms))
     if rc:
-        raise RuntimeError(f"tgp_smem_atomic failed: cudaError {rc}")
-    return {"random": bool(random), "atomics_per_s": rate.value, "ms_per_launch": ms.value}
+        raise RuntimeError(f"tgp_smem_atomic_kind failed: cudaError {rc}")
+    return {"kind": kind, "random": bool(random), "atomics_per_s": rate.value, "ms_per_launch": ms.value}
 
 
 def gather_rates() -> dict:
@@ -65,7 +67,13 @@ def gather_rates() -> dict:
     return {"l2_sector": sector_gather(64 << 20), "hbm_sector": sector_gather(2 << 30, reps=3),
             "tex_coherent": tex_gather(512, 512, 64, True), "tex_random": tex_gather(512, 512, 64, False),
             "tex_coherent_l1": tex_gather(64, 64, 4, True), "tex_random_l1": tex_gather(64, 64, 4, False),
-            "smem_atomic_conflict_free": smem_atomic(False), "smem_atomic_random": smem_atomic(True)}
+            "smem_atomic_conflict_free": smem_atomic(False), "smem_atomic_random": smem_atomic(True),
+            "smem_atomic_u64_conflict_free": smem_atomic(False, kind="u64"),
+            "smem_atomic_u64_random": smem_atomic(True, kind="u64"),
+            "smem_atomic_f32_conflict_free": smem_atomic(False, kind="f32"),
+            "smem_atomic_f32_random": smem_atomic(True, kind="f32"),
+            "smem_load_conflict_free": smem_atomic(False, kind="load"),
+            "smem_load_random": smem_atomic(True, kind="load")}
 
 
 if __name__ == "__main__":

@@ -44,7 +44,7 @@ def test_probe_library_exports_its_header():
     build.build()
     text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "tg_probe.h")).read(), flags=re.S)
     names = sorted(set(re.findall(r"\b(tgp_[a-z0-9_]+)\s*\(", text)))
-    assert names == ["tgp_sector_gather", "tgp_smem_atomic", "tgp_tex_gather"]
+    assert names == ["tgp_sector_gather", "tgp_smem_atomic", "tgp_smem_atomic_kind", "tgp_tex_gather"]
     lib = probe.load()
     for name in names:
         assert hasattr(lib, name), name

@@ -299,3 +299,24 @@ def test_batched_operators_split_into_chunks():
         assert torch.equal(bb[vo:vo + v.size].view(g.vol_shape), tg.backproject(g, pt, "matched"))
         po += p.size
         vo += v.size
+
+
+def test_matched_backprojection_propagates_non_finite_data():
+    """One Inf and one NaN pixel: the FP64 oracle makes the voxels those rays
+    touch non-finite; the fixed-point GPU transpose, which has no scale for
+    such data, returns NaN in every voxel (a superset), and CGLS on the same
+    data returns NaN instead of finite-looking values."""
+    g = ragged_geometry(13)
+    y = inputs.random_projections(g, seed=14)
+    y[2, 10, 20] = np.inf
+    y[5, 7, 3] = np.nan
+    ref = oracle.backproject(g, y, "matched")
+    bad_ref = ~np.isfinite(ref)
+    assert bad_ref.any() and not bad_ref.all()
+    got = host(tg.backproject(g, dev(y), "matched"))
+    assert np.isnan(got).all()
+    yb = dev(np.stack([inputs.random_projections(g, seed=15), y]))
+    both = host(tg.backproject(g, yb, "matched"))
+    assert np.isnan(both[1]).all()
+    assert_vol_close(both[0], oracle.backproject(g, inputs.random_projections(g, seed=15), "matched"))
+    assert np.isnan(host(tg.cgls(g, dev(y), 2))).all()
