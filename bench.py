@@ -11,6 +11,9 @@ C ABI:
   * tg_cgls, one iteration from x0 = 0 (two interpolated forward
     projections, two matched backprojections, fused FP64 inner products and
     vector updates),
+  * tg_ossart, one iteration from x0 = 0 with blocks of 20 angles (the SIRT
+    weights W = 1/(A 1) and V_s = 1/(A_s^T 1), then one sweep over the 36
+    blocks: a projection and a backprojection each),
   * tg_forward with the Siddon projector,
   * tg_fdk (cosine weight + Ram-Lak filter + FDK backprojection).
 Units: forward samples (trilinear samples taken, or Siddon voxel segments)
@@ -117,7 +120,7 @@ def bench_config(case, world):
     return {"workload": CASES[case][0], "parallelism": "replicas" if world > 1 else "single",
             "l2": "inputs (2.8 GB) exceed L2 (129 MB); no flush" if case == "clinical"
             else "inputs (0.35 GB) exceed L2 (129 MB); no flush",
-            "step": "tg_cgls 1 iteration + tg_forward(siddon) + tg_fdk"}
+            "step": "tg_cgls 1 iteration + tg_ossart 1 iteration (blocks of 20) + tg_forward(siddon) + tg_fdk"}
 
 
 def make_inputs(case="clinical", seed=1):
@@ -324,12 +327,16 @@ def run_gpu(args):
     s_interp = tg.count_samples(g, "interp")
     s_siddon = tg.count_samples(g, "siddon")
     bp_pairs = vol_elems * g.nAngles
-    units_cgls = 2 * s_interp + 2 * bp_pairs
-    units_step = units_cgls + s_siddon + bp_pairs
+    units_cgls = 2 * s_interp + 2 * bp_pairs      # initial s = A^T r, then q = A p and s = A^T r
+    units_ossart = 2 * s_interp + 2 * bp_pairs    # W = 1/(A 1), V_s = 1/(A_s^T 1), one sweep
+    units_step = units_cgls + units_ossart + s_siddon + bp_pairs
+    xo = torch.zeros(g.vol_shape, device=dev)
 
     def step():
         xw.zero_()
         tg.cgls(g, b, 1, x0=xw)
+        xo.zero_()
+        tg.ossart(g, b, 1, blocksize=20, x0=xo)
         tg.forward(g, x, "siddon", out=p_sid)
         tg.fdk(g, b, out=v_fdk)
 
@@ -383,14 +390,18 @@ def run_gpu(args):
     bh = torch.from_numpy(b_np).pin_memory()
     xh = torch.from_numpy(x_np).pin_memory()
     xwh = torch.zeros(g.vol_shape).pin_memory()
+    xoh = torch.zeros(g.vol_shape).pin_memory()
     sidh = torch.empty(g.proj_shape).pin_memory()
     fdkh = torch.empty(g.vol_shape).pin_memory()
-    h2d = 4 * (proj_elems + vol_elems) + 4 * vol_elems + 4 * proj_elems     # cgls (b, x0), siddon (x), fdk (b)
-    d2h = 4 * vol_elems + 4 * proj_elems + 4 * vol_elems                    # cgls x, siddon proj, fdk vol
+    # cgls (b, x0), ossart (b, x0), siddon (x), fdk (b)
+    h2d = 2 * 4 * (proj_elems + vol_elems) + 4 * vol_elems + 4 * proj_elems
+    d2h = 2 * 4 * vol_elems + 4 * proj_elems + 4 * vol_elems                # cgls x, ossart x, siddon proj, fdk vol
 
     def step_host():
         xwh.zero_()
         tg.cgls(g, bh, 1, x0=xwh)
+        xoh.zero_()
+        tg.ossart(g, bh, 1, blocksize=20, x0=xoh)
         tg.forward(g, xh, "siddon", out=sidh)
         tg.fdk(g, bh, out=fdkh)
 
@@ -403,16 +414,26 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     secs_e2e = max_over_ranks(time.perf_counter() - t0, world)
     e2e = replica_value(units_step, args.steps, secs_e2e, world)
-    del bh, xh, xwh, sidh, fdkh
+    del bh, xh, xwh, xoh, sidh, fdkh
 
-    # average launch durations inside the timed region (tg_kernel_timing)
-    avg = {k: (ms * 1e-3 / n if n else None) for k, (ms, n) in kt.items()}
-    t_bp_live = avg["bp_matched"] or t_bp
-    t_fp_live = avg["fp_interp"] or t_fp
+    # device time of each kernel class inside the timed region (tg_kernel_timing)
+    # and the units those launches processed: per step, the interpolated
+    # projector runs 4 full projections (CGLS: r0 and q; OS-SART: W and one
+    # sweep), the fixed-point transpose 2 (CGLS) and the split transpose 2
+    # (OS-SART: V_s and one sweep)
     rates = _probe_rates()
-    roof = roofline_bp(s_interp, t_bp_live, rates)
-    roof_fp = roofline_fp(s_interp, t_fp_live, rates)
-    both = (s_interp / roof_fp["peak_samples_per_s"] + s_interp / roof["peak_samples_per_s"])
+    per_step_samples = {"fp_interp": 4 * s_interp, "bp_matched": 2 * s_interp, "bp_matched_split": 2 * s_interp}
+    roofs = {}
+    for name, fn in (("fp_interp", roofline_fp), ("bp_matched", roofline_bp), ("bp_matched_split", roofline_bp_split)):
+        ms, n = kt[name]
+        if n:
+            roofs[name] = fn(per_step_samples[name] * args.steps, ms * 1e-3, rates)
+            roofs[name]["launches_in_timed_region"] = n
+    dominant = max(roofs, key=lambda k: kt[k][0])
+    roof = dict(roofs[dominant])
+    t_fp_live = kt["fp_interp"][0] * 1e-3 / (4 * args.steps)
+    t_bp_live = kt["bp_matched"][0] * 1e-3 / (2 * args.steps)
+    both = (s_interp / roofs["fp_interp"]["peak_samples_per_s"] + s_interp / roofs["bp_matched"]["peak_samples_per_s"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -421,12 +442,12 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": roof,
-            "roofline_fp": roof_fp,
-            "roofline_fp_bp": {"kernels": "k_fp_interp_tex + k_bp_matched (one A and one A^T)",
+            "rooflines": roofs,
+            "roofline_fp_bp": {"kernels": "k_fp_interp_tex + k_bp_mx fixed point (one A and one A^T)",
                                "achieved_s": t_fp_live + t_bp_live, "roofline_s": both,
                                "frac": both / (t_fp_live + t_bp_live)},
-            "kernels_in_timed_region": {k: {"launches": n, "total_ms": ms, "avg_ms": (ms / n if n else None)}
-                                        for k, (ms, n) in kt.items()},
+            "kernels_in_timed_region": {k: {"launches": n, "total_ms": ms, "share_of_step": ms * 1e-3 / secs,
+                                            "avg_ms": (ms / n if n else None)} for k, (ms, n) in kt.items()},
             "kernels_s": {"fp_interp": t_fp, "bp_matched": t_bp, "fp_siddon": t_sid, "bp_fdk": t_bpf,
                           "fdk": t_fdk},
             "rates": {"fp_interp_samples_per_s": s_interp / t_fp_live, "bp_matched_samples_per_s": s_interp / t_bp_live,
@@ -437,7 +458,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and args.learned_pretrain + args.learned_finetune > 0:
         # the second half of the metric: seconds to PSNR, learned vs CGLS, after
         # a shortened training pass (its budget is stated in the object)
-        del x, xw, p_sid, v_fdk, b
+        del x, xw, xo, p_sid, v_fdk, b
         torch.cuda.empty_cache()
         line["learned"] = learned_measure(args.learned_pretrain, args.learned_finetune, 1, ragged=False)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -469,13 +490,26 @@ def roofline_bp(samples, t, rates):
     with conflict-free addresses (one 32-lane wavefront per clock)."""
     peak = rates["smem_atomic_conflict_free"] / 8.0
     achieved = samples / t
-    return {"bound": "smem_atomic", "kernel": "k_bp_matched", "achieved": achieved / 1e9, "peak": peak / 1e9,
+    return {"bound": "smem_atomic", "kernel": "k_bp_mx (fixed point)", "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "Gsamples/s", "frac": achieved / peak, "traffic": BP_TRAFFIC_PER_LAUNCH,
             "peak_samples_per_s": peak,
             "peak_source": "measured conflict-free shared-memory 32-bit atomic adds (libtgprobe tgp_smem_atomic) / "
                            "8 atomics per sample",
             "random_scatter_peak": rates["smem_atomic_random"] / 8.0 / 1e9,
             "unit_of_work": "one trilinear sample of the interpolated projector (8 contributions)"}
+
+
+def roofline_bp_split(samples, t, rates):
+    """k_bp_mx with split accumulation (SIRT / OS-SART / EM epilogues): every
+    product goes to two fixed-point words, 16 atomics per sample."""
+    peak = rates["smem_atomic_conflict_free"] / 16.0
+    achieved = samples / t
+    return {"bound": "smem_atomic", "kernel": "k_bp_mx (split words)", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "Gsamples/s", "frac": achieved / peak, "traffic": None, "peak_samples_per_s": peak,
+            "peak_source": "measured conflict-free shared-memory 32-bit atomic adds (libtgprobe tgp_smem_atomic) / "
+                           "16 atomics per sample",
+            "random_scatter_peak": rates["smem_atomic_random"] / 16.0 / 1e9,
+            "unit_of_work": "one trilinear sample of the interpolated projector (8 contributions, two words each)"}
 
 
 def roofline_fp(samples, t, rates):
@@ -513,9 +547,12 @@ def learned_measure(pretrain, finetune, n_eval, ragged=True, log=None):
     net = L.LearnedGradient(seed=0).to(dev)
     g64, g256 = inputs.config_learned(64), inputs.config_learned(256)
     l_pre = L.train(net, g64, range(1000, 1000 + 2 * pretrain), steps=10, batch=2, lr=3e-4) if pretrain else []
+    torch.cuda.synchronize()
+    t_ft0 = time.perf_counter()
     l_ft = L.train(net, g256, range(3000, 3000 + finetune), steps=10, batch=1, lr=1e-4) if finetune else []
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t_start
+    s_per_phantom = (time.perf_counter() - t_ft0) / finetune if finetune else None
     eta = 1.0 / L.operator_norm_sq(g256, device=dev)
     rows = []
     for k in range(n_eval):
@@ -558,7 +595,9 @@ def learned_measure(pretrain, finetune, n_eval, ragged=True, log=None):
     out = {"workload": "256^3 at 1 mm, 60 angles over 2pi, 512x512 detector at 0.8 mm, 20-ellipsoid phantoms, "
                        "Poisson noise I0=1e4; learned gradient 10 steps, 5x conv3d 3^3 32 ch (BF16, FP32 acc)",
            "training": {"pretrain_64_batches_of_2": pretrain, "finetune_256_phantoms": finetune,
-                        "seconds": t_train, "loss_first": l_pre[:3], "loss_last": (l_ft or l_pre)[-3:]},
+                        "seconds": t_train, "seconds_per_256_phantom": s_per_phantom,
+                        "projected_seconds_2000_phantoms_256": 2000 * s_per_phantom if s_per_phantom else None,
+                        "loss_first": l_pre[:3], "loss_last": (l_ft or l_pre)[-3:]},
            "per_phantom": rows}
     reached = [r["learned_s_to_cgls_psnr"] for r in rows if r["learned_s_to_cgls_psnr"] is not None]
     out["learned_s_to_cgls_psnr"] = float(np.mean(reached)) if rows and len(reached) == len(rows) else None
@@ -756,6 +795,43 @@ def run_micro(args):
     return 0
 
 
+KERNEL_CASES = ("fp_interp", "fp_siddon", "bp_matched", "bp_fdk", "bp_siddon", "fdk_rows_hamming", "tv_march")
+
+
+def run_kernel(args):
+    """The capture workload of one kernel for a profiler (no JSON line):
+    the half-resolution scan (256^3 at 1 mm, 360 views, 384 x 512 detector:
+    inputs above the 129 MB L2, a few GB on the device), one warm-up and one
+    further launch of the named operator; tv_march runs on a 512^3 volume."""
+    import torch
+
+    from paper_2412_10129_gb300 import build, inputs, tg
+    torch.cuda.set_device(0)
+    build.build()
+    tg.load()
+    g = inputs.circular_geometry((256, 256, 256), (1.0,) * 3, (512, 384), (0.8, 0.8), 360, 1000.0, 1536.0)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    b = torch.rand(g.proj_shape, generator=gen, device="cuda")
+    x = torch.rand(g.vol_shape, generator=gen, device="cuda")
+    v = torch.empty(g.vol_shape, device="cuda")
+    p = torch.empty(g.proj_shape, device="cuda")
+    ops = {"fp_interp": lambda: tg.forward(g, x, "interp", out=p),
+           "fp_siddon": lambda: tg.forward(g, x, "siddon", out=p),
+           "bp_matched": lambda: tg.backproject(g, b, "matched", out=v),
+           "bp_fdk": lambda: tg.backproject(g, b, "fdk", out=v),
+           "bp_siddon": lambda: tg.backproject(g, b, "siddon", out=v),
+           "fdk_rows_hamming": lambda: tg.fdk_filter(g, b, "hamming", out=p)}
+    if args.kernel == "tv_march":
+        xt = torch.rand((512, 512, 512), generator=gen, device="cuda")
+        fn = lambda: tg.tv_descent(xt, 1, 1e-3)  # noqa: E731
+    else:
+        fn = ops[args.kernel]
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    return 0
+
+
 def _siddon_gpu(g, x_np, dev):
     import torch
 
@@ -770,7 +846,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tg", choices=["tg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="clinical", choices=sorted(CASES) + ["learned", "solvers", "micro"],
+    ap.add_argument("--kernel", default="bp_matched", choices=KERNEL_CASES,
+                    help="--case kernel: the operator whose capture workload runs")
+    ap.add_argument("--case", default="clinical", choices=sorted(CASES) + ["learned", "solvers", "micro", "kernel"],
                     help="workload; 'medium' is the half-resolution scan used for profiler captures; 'learned' "
                          "trains the learned-gradient scheme and times it against CGLS; 'solvers' times one "
                          "iteration of every solver and the extra operators at 512^3")
@@ -786,6 +864,8 @@ def main():
         return run_learned(args) if args.impl != "reference" else 0
     if args.case == "micro":
         return run_micro(args) if args.impl != "reference" else 0
+    if args.case == "kernel":
+        return run_kernel(args) if args.impl != "reference" else 0
     if args.case == "solvers":
         args.case = "clinical"
         return run_solvers(args) if args.impl != "reference" else 0

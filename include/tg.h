@@ -221,8 +221,12 @@ tg_status tg_fdk_ex(const tg_geometry *geo, const double *angles, int nAngles, c
 tg_status tg_fdk_filter(const tg_geometry *geo, const double *angles, int nAngles, const float *proj,
                         float *out, int filter, int weights, void *stream);
 
-/* SIRT (Sec. 2.1): x <- P(x + lambda V A^T W (b - A x)), W = 1/(A 1),
- * V = 1/(A^T 1) (0 where the sum is 0), P = clamp at 0 when nonneg != 0.
+/* SIRT (Sec. 2.1): x <- P(x + lambda V A^T W (b - A x)), W = 1/(A 1)
+ * (0 where the sum is 0), V = 1/(A^T 1) (0 where the sum is below 1e-3
+ * delta, delta the TG_INTERP sample step: a voxel covered by less than a
+ * thousandth of one sample counts as unseen), P = clamp at 0 when
+ * nonneg != 0.  The backprojections accumulate in 32-bit fixed point with
+ * every product split over two words (deterministic).
  * A = TG_INTERP, A^T = TG_MATCHED.  vol holds x0 on entry and x on exit.
  * resid_hist (nullable, host or device, niter doubles) receives
  * ||A x_k - b|| after each iteration (one extra projection per iteration);
@@ -359,11 +363,13 @@ tg_status tg_device_status(void *stream);
 enum {
     TG_KT_FP_INTERP = 0,   /* interpolated projector (TG_INTERP) */
     TG_KT_FP_SIDDON = 1,   /* Siddon projector */
-    TG_KT_BP_MATCHED = 2,  /* matched transpose of TG_INTERP (brick scatter) */
+    TG_KT_BP_MATCHED = 2,  /* matched transpose of TG_INTERP (brick scatter), one fixed-point word a product */
     TG_KT_BP_FDK = 3,      /* FDK-weighted backprojection */
     TG_KT_BP_SIDDON = 4,   /* transpose of the Siddon projector */
     TG_KT_FDK_FILTER = 5,  /* FDK row filter */
-    TG_KT_COUNT = 6
+    TG_KT_BP_MATCHED_SPLIT = 6, /* the matched transpose of the SIRT / EM family: each product split
+                                   over two fixed-point words */
+    TG_KT_COUNT = 7
 };
 tg_status tg_kernel_timing(int enable);
 tg_status tg_kernel_timing_read(int kernel_class, double *ms, uint64_t *launches);
@@ -382,7 +388,8 @@ tg_status tg_test_conv_wait(int stall, long long budget_cycles);
 
 /* MLEM (Sec. 2.1, Eq. 5; statistical methods): x <- x V A^T (b / (A x)),
  * V = 1/(A^T 1), the Kullback-Leibler / Poisson-likelihood counterpart of
- * Eq. 4.  A ray with A x = 0 contributes 0; a voxel with A^T 1 = 0 keeps its
+ * Eq. 4.  A ray with A x = 0 contributes 0; a voxel with A^T 1 below
+ * 1e-3 delta (as for tg_sirt) keeps its
  * value.  method TG_INTERP uses (TG_INTERP, TG_MATCHED), TG_SIDDON uses
  * (TG_SIDDON, TG_SIDDON_BP).  vol holds x0 on entry (positive; x0 = 1 is
  * the usual start) and x on exit.  resid_hist as for tg_sirt. */

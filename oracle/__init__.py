@@ -254,12 +254,36 @@ def _safe_inv(a: np.ndarray) -> np.ndarray:
     return out
 
 
+# A voxel whose column sum A^T 1 (over the angles of a block) is below this
+# fraction of one full-weight sample's (delta = accuracy * min(dVoxel)) counts
+# as unseen by the block: V = 0 for SIRT / OS-SART, and it keeps its value in
+# MLEM / OS-EM.  Below it V A^T r is a 0/0 limit that the position rounding of
+# any FP32 implementation decides (the reading of the column normalisation of
+# the Kaczmarz-type and statistical methods, Sec. 2.1).
+COVERAGE_MIN = 1e-3
+
+
+def coverage_floor(geo) -> float:
+    """COVERAGE_MIN times the interpolated projector's sample step (mm)."""
+    acc = float(geo.accuracy) if geo.accuracy > 0 else 0.5
+    return COVERAGE_MIN * acc * float(min(geo.dVoxel))
+
+
+def _column_inv(a: np.ndarray, floor: float) -> np.ndarray:
+    """1 / a where a >= floor, else 0."""
+    out = np.zeros_like(a)
+    seen = a >= floor
+    out[seen] = 1.0 / a[seen]
+    return out
+
+
 def sirt_weights(geo):
-    """W = 1/(A 1) per ray and V = 1/(A^T 1) per voxel, 0 where the sum is 0."""
+    """W = 1/(A 1) per ray (0 where the sum is 0) and V = 1/(A^T 1) per
+    voxel (0 where the sum is below coverage_floor)."""
     nx, ny, nz = (int(v) for v in geo.nVoxel)
     nu, nv = (int(v) for v in geo.nDetector)
     W = _safe_inv(forward(geo, np.ones((nz, ny, nx))))
-    V = _safe_inv(backproject(geo, np.ones((geo.nAngles, nv, nu)), "matched"))
+    V = _column_inv(backproject(geo, np.ones((geo.nAngles, nv, nu)), "matched"), coverage_floor(geo))
     return W, V
 
 
@@ -398,8 +422,8 @@ def osem(geo, b, niter: int, blocksize: int, x0=None, method: str = "interp", or
         x <- x / (A_s^T 1) * A_s^T (b_s / (A_s x)),
     the MLEM update of Eq. 5 restricted to the block (Eq. 5's normalisation
     is the backprojection of ones, the sensitivity of each voxel).  A ray
-    with A_s x = 0 contributes 0; a voxel the block does not see
-    (A_s^T 1 = 0) keeps its value.  x0 = 1 unless given.  ``method``
+    with A_s x = 0 contributes 0; a voxel the block does not see (A_s^T 1
+    below coverage_floor) keeps its value.  x0 = 1 unless given.  ``method``
     picks the pair (A, A^T): interpolated + matched, or Siddon + its
     transpose.  Returns (x, ||A x_k - b|| after each iteration)."""
     fp, bp = _EM_PAIRS[method]
@@ -409,12 +433,13 @@ def osem(geo, b, niter: int, blocksize: int, x0=None, method: str = "interp", or
     blocks = subsets(geo.nAngles, blocksize)
     sub = [geo.subset(idx) for idx in blocks]
     sens = [backproject(g, np.ones(g.proj_shape), bp) for g in sub]
+    floor = coverage_floor(geo)
     hist = []
     for perm in block_orders(len(blocks), niter, order, seed):
         for q in perm:
             idx, g, sv = blocks[q], sub[q], sens[q]
             ratio = _safe_div(b[idx], forward(g, x, fp))
-            x = np.where(sv != 0, x * _safe_inv(sv) * backproject(g, ratio, bp), x)
+            x = np.where(sv >= floor, x * _column_inv(sv, floor) * backproject(g, ratio, bp), x)
         hist.append(float(np.linalg.norm(forward(geo, x, fp) - b)))
     return x, np.array(hist)
 

@@ -6,8 +6,8 @@ The compute path is the CUDA library ``libtg`` (``csrc/``, C ABI declared in
 only; the library is loaded on first use).  ``inputs`` draws seeded
 synthetic scans and phantoms; ``autograd`` wraps the projector pair as
 ``torch.autograd.Function``s; ``learned`` is the learned-gradient scheme;
-``build`` compiles the library in-tree; ``profile_cases`` holds the small
-workloads of the profiler captures.
+``build`` compiles the library in-tree; ``probe`` measures the gather and
+scatter rates the projectors are reported against.
 """
 from . import inputs, tg  # noqa: F401
 

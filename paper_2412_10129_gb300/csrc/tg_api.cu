@@ -185,7 +185,7 @@ struct Sart {
             e.absmax = amax;
             e.fp32_acc = 1;
             c.ok(launch_backproject(TG_MATCHED, gs, dA + blocks[k].start, ones, V + k * nvox, 1, BP_STORE, e, c.s));
-            c.ok(launch_safe_inverse(V + k * nvox, nvox, c.s));
+            c.ok(launch_column_inverse(V + k * nvox, nvox, coverage_floor(g), c.s));
         }
     }
 
@@ -398,7 +398,7 @@ tg_status em_family(const tg_geometry *geo, const double *angles, int nA, const 
         e.absmax = amax;
         e.fp32_acc = 1;
         c.ok(launch_backproject(bpm, gs, dA + blocks[k].start, ones, V + k * nvox, 1, BP_STORE, e, c.s));
-        c.ok(launch_safe_inverse(V + k * nvox, nvox, c.s));
+        c.ok(launch_column_inverse(V + k * nvox, nvox, coverage_floor(g), c.s));
     }
     const size_t plane = (size_t)g.nu * g.nv;
     uint64_t rng = seed;

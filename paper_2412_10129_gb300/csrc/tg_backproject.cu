@@ -5,33 +5,37 @@
 // delta * y_i * w to the eight voxels its trilinear interpolation reads,
 // with the same weights w.
 //
-// It runs brick by brick.  A CTA owns a brick of BX x BY x BZ voxels and,
-// for every angle, visits the rays whose samples can touch it (the
-// detector bounding box of the brick grown by one voxel, the reach of a
-// trilinear footprint).  Each ray is rebuilt with the forward kernel's FP32
-// set-up, so the sample positions are bit-identical, and each sample
-// scatters its eight weighted contributions into shared memory.  Shared
-// float atomics are read-modify-write loops on this GPU, but 32-bit integer
-// atomics run at one warp instruction per clock, so the contributions are
-// accumulated in 32-bit fixed point: y is scaled so that no flush period
-// can overflow (the scale comes from max |y| over the call and a geometric
-// bound on one voxel's summed weights per projection), each product is
-// rounded to an integer with the 1.5 * 2^23 addend, and after every angle
-// the owned accumulators are converted and added to FP32 registers (a
-// one-angle period keeps the scale as fine as the bound allows; the flush
-// costs about 1 % of the work of an angle).
-// Integer sums do not depend on the order of the atomics, so the result is
-// deterministic; the rounding costs ~1e-6 of max |y| per product, random in
-// sign.  A warp's 32 rays are taken four pixels apart in u and v, so their
-// samples rarely share an accumulator (bank) in one instruction.  Only
-// bricks on the volume boundary need the rays' box-membership walk.
+// It runs brick by brick.  A CTA owns a brick of voxels and, for every
+// angle, visits the rays whose samples fall in its cells (detector bounding
+// box of the brick, then an exact per-ray sample interval).  Each ray is
+// rebuilt with the forward kernel's FP32 set-up, so the sample positions are
+// bit-identical, and each sample scatters its eight weighted contributions
+// into shared memory.  Shared float atomics are read-modify-write loops on
+// this GPU (measured: 8.3e11 random FP32 adds/s against 2.8e12 for 32-bit
+// integers), so the contributions are accumulated in 32-bit fixed point: y
+// is scaled so that one angle's sums cannot overflow (the scale comes from
+// max |y| over the call and a geometric bound on one voxel's summed weights
+// per projection), each product is rounded to an integer with the
+// 1.5 * 2^23 addend, and after every angle the accumulators are converted
+// and added to FP32 registers.  Integer sums do not depend on the order of
+// the atomics, so the result is deterministic.
+//
+// Two brick kernels:
+//   k_bp_mx (the default): exclusive cells -- every sample is processed by
+//     the one brick owning its cell; contributions to the brick's upper
+//     faces go to a rim buffer that a merge kernel adds to the neighbours'
+//     sums in a fixed order before the epilogue (scratch: the rim buffer,
+//     and a volume for the modes that read the output).  Lanes take rays
+//     from a per-angle list (long rays first) through a work queue.
+//   k_bp_matched: bricks grown by a two-voxel rim, every sample of the rim
+//     processed by both bricks (1.27 times the samples), no scratch beyond
+//     one word per batch item: used where the call must not allocate
+//     (tg_backproject_noalloc) or a compact ray record would overflow.
 //
 // TG_FDK_WEIGHT is the FDK backprojection (Sec. 2.1, direct methods):
 //     x_j = (pi / nAngles) sum_a (DSO / L_ja)^2 bilinear(p_a, u_ja, v_ja).
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
-#include <string>
 
 #include "tg_internal.cuh"
 #include "tg_ray.cuh"
@@ -239,33 +243,6 @@ __device__ __forceinline__ void scatter_sample(unsigned int *accc, int k, float 
     }
 }
 
-// 64-bit fixed point: each contribution is its FP32 product (ys already
-// carries the power-of-two scale) rounded to an integer, added with a 64-bit
-// integer atomic; the sums are exact and order-independent, and a product
-// keeps FP32 relative precision down to 2^-62 of the scale's range.
-__device__ __forceinline__ void scatter_sample64(unsigned long long *accc, int k, float gx, float gy, float gz,
-                                                 float sx, float sy, float sz, float ys, int ox, int oy, int oz) {
-    const float kf = (float)k;
-    const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
-    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
-    const int lx = min(max((int)fx - ox, 0), RX - 2);
-    const int ly = min(max((int)fy - oy, 0), RY - 2);
-    const int lz = min(max((int)fz - oz, 0), RZ - 2);
-    const float wx = x - fx, wy = yy - fy, wz = z - fz;
-    const float c0 = ys * (1.f - wz), c1 = ys * wz;
-    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
-    const float ux = 1.f - wx;
-    unsigned long long *c = accc + lz * PP + ly * PX + lx;
-    atomicAdd(c, (unsigned long long)__float2ll_rn(b00 * ux));
-    atomicAdd(c + 1, (unsigned long long)__float2ll_rn(b00 * wx));
-    atomicAdd(c + PX, (unsigned long long)__float2ll_rn(b01 * ux));
-    atomicAdd(c + PX + 1, (unsigned long long)__float2ll_rn(b01 * wx));
-    atomicAdd(c + PP, (unsigned long long)__float2ll_rn(b10 * ux));
-    atomicAdd(c + PP + 1, (unsigned long long)__float2ll_rn(b10 * wx));
-    atomicAdd(c + PP + PX, (unsigned long long)__float2ll_rn(b11 * ux));
-    atomicAdd(c + PP + PX + 1, (unsigned long long)__float2ll_rn(b11 * wx));
-}
-
 // F32: accumulate with FP32 shared atomics instead (read-modify-write loops,
 // ~2x slower here; the sums then depend on the order of the atomics at the
 // 1e-7 level).  Chosen where each voxel's sum must keep its own relative
@@ -275,7 +252,7 @@ __device__ __forceinline__ void scatter_sample64(unsigned long long *accc, int k
 // One brick (bx, by, bz) of one volume: pb are the volume's projections,
 // vb its output (and the SIRT weight's) voxels, gmax its max |y|; the
 // epilogue writes vb directly and adds the FP64 norm to ep.norm[0].
-template <int MODE, bool F32, bool PAR, bool I64 = false>
+template <int MODE, bool F32, bool PAR>
 __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, float *__restrict__ vb,
                                                  const Angle *__restrict__ angles, const Grid &g, const BpEpilogue &ep,
                                                  float gmax, int bx, int by, int bz) {
@@ -294,16 +271,10 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     RayRec *rays = reinterpret_cast<RayRec *>(acc + 2 * ACC_WORDS);
     __shared__ int s_cnt[2];  // rays listed, rays handed out
     const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
-    float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
-    if (I64 && scale > 0.f) {
-        // 2^E with gmax 2^E wbound FLUSH <= 2^62: one flush period's sums fit 63 bits
-        const float e = floorf(62.f - log2f(gmax) - log2f(g.wbound * (float)FLUSH));
-        scale = exp2f(fminf(fmaxf(e, -120.f), 120.f));
-    }
+    const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
     const float inv_scale = scale > 0.f ? 1.f / scale : 0.f;
     const float scale_f = FINE * scale, inv_scale_f = inv_scale * (1.f / FINE);
-    const float ybig = I64 ? -1.f : gmax * (1.f / FINE);  // 64-bit: one class (every ray "big")
-    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
+    const float ybig = gmax * (1.f / FINE);
     // owned voxel j of this thread: (lane, warp + 16 (j & 1), j >> 1)
     const int obase = RIM * PP + (warp + RIM) * PX + lane + RIM;
     const int ox = x0 - RIM, oy = y0 - RIM, oz = z0 - RIM;  // voxel of accumulator cell (0, 0, 0)
@@ -313,7 +284,7 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     for (int i = tid; i < 2 * ACC_WORDS; i += MT) acc[i] = 0u;
     __syncthreads();
     // Inf or NaN in the data: no fixed-point scale exists; every voxel is NaN
-    const bool nonfinite = !F32 && !(gmax <= 3.4028235e38f);  // (fixed point, 32- or 64-bit)
+    const bool nonfinite = !F32 && !(gmax <= 3.4028235e38f);
     for (int a0 = 0; a0 < (nonfinite ? 0 : g.nA); a0 += FLUSH) {
         const int a1 = min(a0 + FLUSH, g.nA);
         for (int a = a0; a < a1; ++a) {
@@ -419,14 +390,8 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
                     // two samples per trip (the second adds zeros past the ray's end)
-                    if (I64) {
-                        scatter_sample64(acc64, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
-                        scatter_sample64(acc64, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
-                    } else {
-                        scatter_sample<F32>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
-                        scatter_sample<F32>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy,
-                                            oz);
-                    }
+                    scatter_sample<F32>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
+                    scatter_sample<F32>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy, oz);
                     k += 2;
                 }
                 __syncthreads();  // the list is refilled by the next chunk
@@ -437,10 +402,7 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
 #pragma unroll
         for (int j = 0; j < OWN; ++j) {
             const int o = obase + (j >> 1) * PP + (j & 1) * 16 * PX;
-            if (I64) {
-                own[j] = fmaf(__ll2float_rn((long long)acc64[o]), inv_scale, own[j]);
-                acc64[o] = 0ull;
-            } else if (F32) {
+            if (F32) {
                 float *af = reinterpret_cast<float *>(acc);
                 own[j] += af[o];
                 af[o] = 0.f;
@@ -478,64 +440,114 @@ __device__ __forceinline__ void bp_matched_brick(const float *__restrict__ pb, f
     if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
 }
 
-// The same contributions as scatter_sample (bit for bit): the sample index
-// arrives as an exact float, and the integral float floor(x) becomes an int
-// through the 1.5 * 2^23 addend (exact for |x| < 2^22) instead of a
-// float-to-int conversion; mo* = MAGIC_BITS + o*.
-__device__ __forceinline__ void scatter_sample_fx(unsigned int *accc, float kf, float gx, float gy, float gz,
-                                                  float sx, float sy, float sz, float ys, int mox, int moy,
-                                                  int moz) {
-    const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
-    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
-    const int lx = min(max(__float_as_int(fx + MAGIC) - mox, 0), RX - 2);
-    const int ly = min(max(__float_as_int(fy + MAGIC) - moy, 0), RY - 2);
-    const int lz = min(max(__float_as_int(fz + MAGIC) - moz, 0), RZ - 2);
-    const float wx = x - fx, wy = yy - fy, wz = z - fz;
-    const float c0 = ys * (1.f - wz), c1 = ys * wz;
-    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
-    const float ux = 1.f - wx;
-    unsigned int *c = accc + lz * PP + ly * PX + lx;
-    atomicAdd(c, fixq(b00, ux));
-    atomicAdd(c + 1, fixq(b00, wx));
-    atomicAdd(c + PX, fixq(b01, ux));
-    atomicAdd(c + PX + 1, fixq(b01, wx));
-    atomicAdd(c + PP, fixq(b10, ux));
-    atomicAdd(c + PP + 1, fixq(b10, wx));
-    atomicAdd(c + PP + PX, fixq(b11, ux));
-    atomicAdd(c + PP + PX + 1, fixq(b11, wx));
+template <int MODE, bool F32, bool PAR>
+__global__ void __launch_bounds__(MT, 1)
+    k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
+                 BpEpilogue ep, int nbx, int nby) {
+    const int bl = blockIdx.x, b = blockIdx.y;
+    BpEpilogue e = ep;
+    if (e.norm) e.norm += b;
+    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    bp_matched_brick<MODE, F32, PAR>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
+                                     __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
 }
 
-template <bool PAR>
-__device__ __noinline__ void ray_frame_outlined(const Angle *A, const Grid *g, int iu, int iv, Ray *r) {
-    float Ld;
-    ray_frame<PAR>(*A, *g, iu, iv, *r, Ld);
-}
-
-// ---- compact-record variant ---------------------------------------------
-// The same scatter with 8-byte ray records (y is read again when a lane
-// takes the ray), so that a list holds RAYCAP8 rays, and two options:
-//   NT  threads per CTA (512 or 1024; each owns BX*BY*BZ/NT voxels),
-//   OG  the owned voxels' FP32 sums live in the output volume instead of
-//       registers (BP_STORE / BP_STORE_NORM: the output is the accumulator),
-//   LF  long rays first: a chunk lists rays of at least LONG_RAY samples
-//       from the front of the list and shorter ones from the back, so the
-//       lane queue hands out the long rays first and the chunk's tail is
-//       made of short ones.
-// Record: iuv = iu | iv << 16; kk = ka | (kc - ka) << 20 | class << 31
-// (ka < 2^20, kc - ka < 2^11: checked on the host).
+// A ray of the current angle with samples in a brick, in 8 bytes: y is read
+// again when a lane takes the ray.  iuv = iu | iv << 16; kk = ka | (kc - ka)
+// << 20 | class << 31 (ka < 2^20, kc - ka < 2^11: checked on the host).
 struct RayRec8 {
     unsigned int iuv;
     unsigned int kk;
 };
-constexpr int RAYCAP8 = 2048;
-constexpr int LONG_RAY = 32;
-constexpr int MATCHED8_SMEM = 2 * ACC_WORDS * 4 + RAYCAP8 * (int)sizeof(RayRec8);
-static_assert(MATCHED8_SMEM <= 232448 - 512, "shared memory of one CTA");
+constexpr int LONG_RAY = 32;  // list order: rays of at least this many samples first
 
+// ---- exclusive-cell bricks ---------------------------------------------------
+// Every sample is processed by exactly one brick: the one owning its
+// trilinear cell (the integer part of its index-space position; a brick
+// owns cells [o, o + B) per axis, brick 0 also the cell -1 below the
+// volume).  A sample's FP32 position, and so its cell, is computed bit for
+// bit alike in every brick, and along a ray the cell index is monotone in
+// the sample index, so a brick's samples of a ray are one interval of k,
+// found from the slab estimate and refined at both ends with the exact
+// rule.  A cell's eight corners are voxels c and c + 1 per axis: the brick's
+// own voxels o .. o + B - 1 and, on its upper faces, voxels o + B that its
+// neighbours own.  Those face ("rim") sums go to a rim buffer and a merge
+// kernel adds them to the owners' sums in a fixed order, then applies the
+// backprojection's epilogue: no sample is processed twice (the rimmed
+// bricks above process 1.27 times the samples), and the result is
+// deterministic.
+// Accumulation kinds:
+//   ACC_FIX   32-bit fixed point, two classes FINE apart by |y| (as
+//             k_bp_matched): one atomic per corner;
+//   ACC_SPLIT 32-bit fixed point in two words per voxel: t = product x
+//             scale, hi = rint(t) in the first, rint((t - hi) 2^m) in the
+//             second (2^m chosen so one angle's sums fit 31 bits): every
+//             product keeps about 2^-(m+21) of max |y| absolute precision,
+//             so voxels whose sums are far below the largest keep their own
+//             relative precision (SIRT / EM divide voxel by voxel), at two
+//             atomics per corner.
+enum { ACC_FIX = 0, ACC_SPLIT = 1 };
+
+template <int XB_, int YB_, int ZB_, int XT_, int RAYCAP_>
+struct Mx {
+    static constexpr int XB = XB_, YB = YB_, ZB = ZB_, XT = XT_, RAYCAP = RAYCAP_;
+    static constexpr int NW = XT / 32;                           // warps
+    static constexpr int YR = YB / NW;                           // owned y rows per warp
+    static constexpr int XA = XB + 2, YA = YB + 2, ZA = ZB + 2;  // accumulator: voxels o - 1 .. o + B
+    static constexpr int PX = XA + 1;                            // row pitch
+    static constexpr int PP = PX * YA + 9;                       // plane pitch
+    static constexpr int WORDS = PP * ZA;                        // 32-bit words of one class
+    static constexpr int F1 = (YB + 1) * (ZB + 1);               // rim face x = o + B
+    static constexpr int F2 = XB * (ZB + 1);                     // rim face y = o + B
+    static constexpr int F3 = XB * YB;                           // rim face z = o + B
+    static constexpr int NRIM = F1 + F2 + F3;
+    static constexpr int RIM_PER_THREAD = (NRIM + XT - 1) / XT;
+    static constexpr int OWN = XB * YB * ZB / XT;                // owned voxels per thread
+    static constexpr int SMEM = 2 * WORDS * 4 + RAYCAP * (int)sizeof(RayRec8);
+    static constexpr int MINB = 1024 / XT;                       // CTAs per SM: 1024 threads at 64 registers
+    static_assert(XB == 32 && NW * YR == YB && OWN == YR * ZB, "owned map: lane = x, warp + NW j = y");
+    static_assert(RAYCAP >= 2 * XT, "a chunk takes at least one full step of candidates");
+    // rim index of accumulator voxel (lx, ly, lz) (local = voxel - o + 1; at
+    // least one coordinate B + 1, the others in 1 .. B + 1) and its inverse
+    __host__ __device__ static int rim_index(int lx, int ly, int lz) {
+        if (lx == XB + 1) return (ly - 1) * (ZB + 1) + (lz - 1);
+        if (ly == YB + 1) return F1 + (lx - 1) * (ZB + 1) + (lz - 1);
+        return F1 + F2 + (lx - 1) * YB + (ly - 1);
+    }
+    __device__ static void rim_local(int r, int &lx, int &ly, int &lz) {
+        if (r < F1) {
+            lx = XB + 1;
+            ly = r / (ZB + 1) + 1;
+            lz = r % (ZB + 1) + 1;
+        } else if (r < F1 + F2) {
+            const int q = r - F1;
+            ly = YB + 1;
+            lx = q / (ZB + 1) + 1;
+            lz = q % (ZB + 1) + 1;
+        } else {
+            const int q = r - F1 - F2;
+            lz = ZB + 1;
+            lx = q / YB + 1;
+            ly = q % YB + 1;
+        }
+    }
+};
+
+// Is sample k (relative to the reference sample) in the cells [lo, hi)?
+__device__ __forceinline__ bool cell_in(const Ray &r, int k, float lox, float loy, float loz, float hix, float hiy,
+                                        float hiz) {
+    const float kf = (float)(k - r.kr);
+    const float cx = floorf(fmaf(kf, r.gx, r.sx)), cy = floorf(fmaf(kf, r.gy, r.sy)),
+                cz = floorf(fmaf(kf, r.gz, r.sz));
+    return cx >= lox && cx < hix && cy >= loy && cy < hiy && cz >= loz && cz < hiz;
+}
+
+// The samples of ray (iu, iv) whose cells lie in [lo, hi) (cell units,
+// exact), as a compact record; false when there are none or y = 0.
 template <bool PAR>
-__device__ __forceinline__ bool region_ray8(const Angle &A, const Grid &g, float yraw, int iu, int iv, bool edge,
-                                            float lox, float loy, float loz, float hix, float hiy, float hiz,
-                                            float ybig, RayRec8 &rec, int &len) {
+__device__ __forceinline__ bool region_ray_x(const Angle &A, const Grid &g, float yraw, int iu, int iv, bool edge,
+                                             float lox, float loy, float loz, float hix, float hiy, float hiz,
+                                             float ybig, RayRec8 &rec, int &len) {
     if (yraw == 0.f) return false;
     Ray r;
     int kb0 = 0, kb1 = 0x7fffffff;
@@ -547,7 +559,7 @@ __device__ __forceinline__ bool region_ray8(const Angle &A, const Grid &g, float
         float Ld;
         ray_frame<PAR>(A, g, iu, iv, r, Ld);
     }
-    float klo = (float)kb0, khi = (float)kb1;
+    float klo = -1e9f, khi = 1e9f;
     const float sv[3] = {r.sx, r.sy, r.sz}, gv[3] = {r.gx, r.gy, r.gz};
     const float lo[3] = {lox, loy, loz}, hi[3] = {hix, hiy, hiz};
     const float kr = (float)r.kr;
@@ -558,12 +570,20 @@ __device__ __forceinline__ bool region_ray8(const Angle &A, const Grid &g, float
             const float ka = fmaf(lo[ax] - sv[ax], ia, kr), kc = fmaf(hi[ax] - sv[ax], ia, kr);
             klo = fmaxf(klo, fminf(ka, kc));
             khi = fminf(khi, fmaxf(ka, kc));
-        } else if (sv[ax] < lo[ax] || sv[ax] >= hi[ax]) {
-            return false;
+        } else {
+            const float c = floorf(sv[ax]);
+            if (c < lo[ax] || c >= hi[ax]) return false;
         }
     }
-    if (!(khi >= klo)) return false;
-    const int ka = max((int)ceilf(klo), kb0), kc = min((int)floorf(khi), kb1);
+    if (!(khi >= klo - 2.f)) return false;
+    int ka = max((int)ceilf(fmaxf(klo, -1e8f)), kb0), kc = min((int)floorf(fminf(khi, 1e8f)), kb1);
+    if (kc < ka - 1) kc = ka - 1;
+    // exact ends (a few steps at most: the slab estimate is within rounding)
+    for (int t = 0; t < 4 && ka > kb0 && cell_in(r, ka - 1, lox, loy, loz, hix, hiy, hiz); ++t) --ka;
+    for (int t = 0; t < 4 && ka <= kc && !cell_in(r, ka, lox, loy, loz, hix, hiy, hiz); ++t) ++ka;
+    if (kc < ka - 1) kc = ka - 1;
+    for (int t = 0; t < 4 && kc < kb1 && cell_in(r, kc + 1, lox, loy, loz, hix, hiy, hiz); ++t) ++kc;
+    for (int t = 0; t < 4 && kc >= ka && !cell_in(r, kc, lox, loy, loz, hix, hiy, hiz); ++t) --kc;
     if (ka > kc) return false;
     const bool big = fabsf(yraw) > ybig;
     rec.iuv = (unsigned int)iu | ((unsigned int)iv << 16);
@@ -572,67 +592,125 @@ __device__ __forceinline__ bool region_ray8(const Angle &A, const Grid &g, float
     return true;
 }
 
-template <int MODE, bool PAR, int NT, bool OG, bool LF, bool FX>
-__device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, float *__restrict__ vb,
-                                                  const Angle *__restrict__ angles, const Grid &g,
-                                                  const BpEpilogue &ep, float gmax, int bx, int by, int bz) {
-    static_assert(!OG || MODE == BP_STORE || MODE == BP_STORE_NORM, "global sums use the output as accumulator");
-    constexpr int NW = NT / 32;                 // warps
-    constexpr int YR = BY / NW;                 // owned y rows per thread
-    constexpr int OWNN = BX * BY * BZ / NT;     // owned voxels per thread
-    static_assert(NW * YR == BY && OWNN == YR * BZ, "owned-voxel map");
+// ACC_SPLIT: the two words of one product (t = p * scale): rint(t) and
+// rint((t - rint(t)) 2^m) (t - rint(t) is exact, |.| <= 1/2)
+__device__ __forceinline__ void split_add(unsigned int *c, int lo_off, float p, float scale, float two_m) {
+    const float t = p * scale;
+    const float r = __fadd_rn(t, MAGIC);
+    const float hi = __fsub_rn(r, MAGIC);
+    atomicAdd(c, (unsigned int)(__float_as_int(r) - MAGIC_BITS));
+    atomicAdd(c + lo_off, (unsigned int)(__float_as_int(fmaf(t - hi, two_m, MAGIC)) - MAGIC_BITS));
+}
+
+// One sample's eight contributions into the exclusive-cell accumulator;
+// mo* = MAGIC_BITS + o* - 1 (local index = voxel - o + 1).
+template <class C, int ACC>
+__device__ __forceinline__ void scatter_x(unsigned int *accc, float kf, float gx, float gy, float gz, float sx,
+                                          float sy, float sz, float ys, int mox, int moy, int moz, float scale,
+                                          float two_m) {
+    const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
+    const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
+    const int lx = min(max(__float_as_int(fx + MAGIC) - mox, 0), C::XB);
+    const int ly = min(max(__float_as_int(fy + MAGIC) - moy, 0), C::YB);
+    const int lz = min(max(__float_as_int(fz + MAGIC) - moz, 0), C::ZB);
+    const float wx = x - fx, wy = yy - fy, wz = z - fz;
+    const float c0 = ys * (1.f - wz), c1 = ys * wz;
+    const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
+    const float ux = 1.f - wx;
+    unsigned int *c = accc + lz * C::PP + ly * C::PX + lx;
+    if (ACC == ACC_SPLIT) {  // ys is the raw y here; each product is split
+        split_add(c, C::WORDS, b00 * ux, scale, two_m);
+        split_add(c + 1, C::WORDS, b00 * wx, scale, two_m);
+        split_add(c + C::PX, C::WORDS, b01 * ux, scale, two_m);
+        split_add(c + C::PX + 1, C::WORDS, b01 * wx, scale, two_m);
+        split_add(c + C::PP, C::WORDS, b10 * ux, scale, two_m);
+        split_add(c + C::PP + 1, C::WORDS, b10 * wx, scale, two_m);
+        split_add(c + C::PP + C::PX, C::WORDS, b11 * ux, scale, two_m);
+        split_add(c + C::PP + C::PX + 1, C::WORDS, b11 * wx, scale, two_m);
+    } else {
+        atomicAdd(c, fixq(b00, ux));
+        atomicAdd(c + 1, fixq(b00, wx));
+        atomicAdd(c + C::PX, fixq(b01, ux));
+        atomicAdd(c + C::PX + 1, fixq(b01, wx));
+        atomicAdd(c + C::PP, fixq(b10, ux));
+        atomicAdd(c + C::PP + 1, fixq(b10, wx));
+        atomicAdd(c + C::PP + C::PX, fixq(b11, ux));
+        atomicAdd(c + C::PP + C::PX + 1, fixq(b11, wx));
+    }
+}
+
+// Reads (and clears) one accumulator voxel as FP32 in units of y; k1, k2 the
+// factors of the first and the second word.
+template <class C>
+__device__ __forceinline__ float take_x(unsigned int *acc, int o, float k1, float k2) {
+    const int v = (int)acc[o], vf = (int)acc[C::WORDS + o];
+    acc[o] = 0u;
+    acc[C::WORDS + o] = 0u;
+    return fmaf((float)v, k1, (float)vf * k2);
+}
+
+// Brick (bx, by, bz) of one volume: pb its projections, sv its owned sums
+// (unscaled, one FP32 per voxel of the volume), rb the brick's NRIM rim
+// sums, gmax the max |y| of its projections.
+template <class C, int ACC, bool PAR>
+__device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__restrict__ sv, float *__restrict__ rb,
+                                         const Angle *__restrict__ angles, const Grid &g, float gmax, int bx, int by,
+                                         int bz) {
     extern __shared__ unsigned int acc[];
+    constexpr int XT = C::XT, NW = C::NW, YR = C::YR;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
-    const float lox = (float)(x0 - 1), loy = (float)(y0 - 1), loz = (float)(z0 - 1);
-    const float hix = (float)(x0 + BX), hiy = (float)(y0 + BY), hiz = (float)(z0 + BZ);
-    const bool edge = x0 == 0 || y0 == 0 || z0 == 0 || x0 + BX >= g.nx || y0 + BY >= g.ny || z0 + BZ >= g.nz;
-    unsigned int *acc_f = acc + ACC_WORDS;
-    RayRec8 *rays = reinterpret_cast<RayRec8 *>(acc + 2 * ACC_WORDS);
-    __shared__ int s_cnt[3];  // long rays listed, rays handed out, short rays listed
-    const float lim = fminf(1073741824.f / (g.wbound * (float)FLUSH), 2097152.f);
-    const float scale = (gmax > 0.f && gmax <= 3.4e38f) ? lim / gmax : 0.f;
+    const int x0 = bx * C::XB, y0 = by * C::YB, z0 = bz * C::ZB;
+    // cells of this brick: [lo, hi) per axis (brick 0 also owns the cell -1)
+    const float lox = (float)(x0 == 0 ? -1 : x0), loy = (float)(y0 == 0 ? -1 : y0), loz = (float)(z0 == 0 ? -1 : z0);
+    const float hix = (float)(x0 + C::XB), hiy = (float)(y0 + C::YB), hiz = (float)(z0 + C::ZB);
+    const bool edge =
+        x0 == 0 || y0 == 0 || z0 == 0 || x0 + C::XB >= g.nx || y0 + C::YB >= g.ny || z0 + C::ZB >= g.nz;
+    RayRec8 *rays = reinterpret_cast<RayRec8 *>(acc + 2 * C::WORDS);
+    __shared__ int s_cnt[3];
+    __shared__ Angle sA;
+    const bool nonfinite = !(gmax <= 3.4028235e38f);
+    const float lim = fminf(1073741824.f / g.wbound, 2097152.f);
+    const float scale = (gmax > 0.f && !nonfinite) ? lim / gmax : 0.f;
     const float inv_scale = scale > 0.f ? 1.f / scale : 0.f;
-    const float scale_f = FINE * scale, inv_scale_f = inv_scale * (1.f / FINE);
-    const float ybig = gmax * (1.f / FINE);
-    const int obase = RIM * PP + (warp + RIM) * PX + lane + RIM;
-    const int ox = x0 - RIM, oy = y0 - RIM, oz = z0 - RIM;
-    const int mox = MAGIC_BITS + ox, moy = MAGIC_BITS + oy, moz = MAGIC_BITS + oz;
-    float own[OG ? 1 : OWNN];
+    // ACC_FIX: the second class is FINE times finer; ACC_SPLIT: the second
+    // word holds fractions of the first's unit at 2^m with 2^(m-1) wbound <= 2^30
+    const float two_m = exp2f(fminf(floorf(31.f - log2f(g.wbound)), 22.f));
+    const float scale_f = ACC == ACC_SPLIT ? 1.f : FINE * scale;
+    const float k1 = inv_scale, k2 = ACC == ACC_SPLIT ? inv_scale / two_m : inv_scale * (1.f / FINE);
+    const float ybig = ACC == ACC_SPLIT ? -1.f : gmax * (1.f / FINE);
+    const int mox = MAGIC_BITS + x0 - 1, moy = MAGIC_BITS + y0 - 1, moz = MAGIC_BITS + z0 - 1;
+    float own[C::OWN], rimv[C::RIM_PER_THREAD];
 #pragma unroll
-    for (int j = 0; j < (OG ? 1 : OWNN); ++j) own[j] = 0.f;
-    for (int i = tid; i < 2 * ACC_WORDS; i += NT) acc[i] = 0u;
-    __syncthreads();
-    const bool nonfinite = !(gmax <= 3.4028235e38f);  // Inf or NaN in the data: every voxel is NaN
-    bool first = true;
-    __shared__ Angle sA;  // the current angle's constants (read by every lane from shared memory)
-    for (int a0 = 0; a0 < (nonfinite ? 0 : g.nA); a0 += FLUSH) {
-        const int a1 = min(a0 + FLUSH, g.nA);
-        for (int a = a0; a < a1; ++a) {
-            __syncthreads();  // every thread is done with the previous angle's constants
-            if (tid < (int)(sizeof(Angle) / sizeof(float4)))
-                reinterpret_cast<float4 *>(&sA)[tid] = __ldg(reinterpret_cast<const float4 *>(angles + a) + tid);
-            __syncthreads();
-            const Angle &A = sA;
-            float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+    for (int j = 0; j < C::OWN; ++j) own[j] = 0.f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float px = (((q & 1) ? hix : lox) + 0.5f - 0.5f * g.nx) * g.dx;
-                const float py = (((q & 2) ? hiy : loy) + 0.5f - 0.5f * g.ny) * g.dy;
-                const float pz = (((q & 4) ? hiz : loz) + 0.5f - 0.5f * g.nz) * g.dz;
-                const float L = fmaf(pz, A.n[2], fmaf(py, A.n[1], px * A.n[0])) - A.Sn;
-                const float Au = fmaf(pz, A.eu[2], fmaf(py, A.eu[1], px * A.eu[0])) - A.Seu;
-                const float Av = fmaf(pz, A.ev[2], fmaf(py, A.ev[1], px * A.ev[0])) - A.Sev;
-                const float iL = 1.f / L;
-                const float fu = fmaf(A.Ku * Au, iL, A.cu), fv = fmaf(A.Kv * Av, iL, A.cv);
-                umin = fminf(umin, fu);
-                umax = fmaxf(umax, fu);
-                vmin = fminf(vmin, fv);
-                vmax = fmaxf(vmax, fv);
-            }
-            const int u0 = max((int)ceilf(umin - 1e-3f), 0), u1 = min((int)floorf(umax + 1e-3f), g.nu - 1);
-            const int v0 = max((int)ceilf(vmin - 1e-3f), 0), v1 = min((int)floorf(vmax + 1e-3f), g.nv - 1);
-            if (u1 < u0 || v1 < v0) continue;
+    for (int j = 0; j < C::RIM_PER_THREAD; ++j) rimv[j] = 0.f;
+    for (int i = tid; i < 2 * C::WORDS; i += XT) acc[i] = 0u;
+    for (int a = 0; a < (nonfinite ? 0 : g.nA); ++a) {
+        __syncthreads();  // the previous angle's constants and list are no longer read
+        if (tid < (int)(sizeof(Angle) / sizeof(float4)))
+            reinterpret_cast<float4 *>(&sA)[tid] = __ldg(reinterpret_cast<const float4 *>(angles + a) + tid);
+        __syncthreads();
+        const Angle &A = sA;
+        // detector bounding box of the positions [lo, hi] (index space)
+        float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float px = (((q & 1) ? hix : lox) + 0.5f - 0.5f * g.nx) * g.dx;
+            const float py = (((q & 2) ? hiy : loy) + 0.5f - 0.5f * g.ny) * g.dy;
+            const float pz = (((q & 4) ? hiz : loz) + 0.5f - 0.5f * g.nz) * g.dz;
+            const float L = fmaf(pz, A.n[2], fmaf(py, A.n[1], px * A.n[0])) - A.Sn;
+            const float Au = fmaf(pz, A.eu[2], fmaf(py, A.eu[1], px * A.eu[0])) - A.Seu;
+            const float Av = fmaf(pz, A.ev[2], fmaf(py, A.ev[1], px * A.ev[0])) - A.Sev;
+            const float iL = 1.f / L;
+            const float fu = fmaf(A.Ku * Au, iL, A.cu), fv = fmaf(A.Kv * Av, iL, A.cv);
+            umin = fminf(umin, fu);
+            umax = fmaxf(umax, fu);
+            vmin = fminf(vmin, fv);
+            vmax = fmaxf(vmax, fv);
+        }
+        const int u0 = max((int)ceilf(umin - 1e-3f), 0), u1 = min((int)floorf(umax + 1e-3f), g.nu - 1);
+        const int v0 = max((int)ceilf(vmin - 1e-3f), 0), v1 = min((int)floorf(vmax + 1e-3f), g.nv - 1);
+        if (u1 >= u0 && v1 >= v0) {
             const float *pa = pb + (size_t)a * g.nv * g.nu;
             const int ntu = (u1 - u0 + 32) >> 5, ntv = (v1 - v0 + 16) >> 4;
             const int ncand = ntu * ntv * 16 * 32;
@@ -654,33 +732,26 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
                         const int iu = u0 + (tile % ntu) * 32 + (slot & 7) * 4 + (ph & 3);
                         const int iv = v0 + (tile / ntu) * 16 + (slot >> 3) * 4 + (ph >> 2);
                         if (iu <= u1 && iv <= v1)
-                            keep = region_ray8<PAR>(A, g, __ldg(pa + (size_t)iv * g.nu + iu), iu, iv, edge, lox, loy,
-                                                    loz, hix, hiy, hiz, ybig, rec, len);
+                            keep = region_ray_x<PAR>(A, g, __ldg(pa + (size_t)iv * g.nu + iu), iu, iv, edge, lox,
+                                                     loy, loz, hix, hiy, hiz, ybig, rec, len);
                     }
-                    if (LF) {
-                        const bool lg = keep && len >= LONG_RAY;
-                        const unsigned ml = __ballot_sync(0xffffffffu, lg);
-                        const unsigned ms = __ballot_sync(0xffffffffu, keep && !lg);
-                        int bl = 0, bs = 0;
-                        if (lane == 0) {
-                            if (ml) bl = atomicAdd(&s_cnt[0], __popc(ml));
-                            if (ms) bs = atomicAdd(&s_cnt[2], __popc(ms));
-                        }
-                        bl = __shfl_sync(0xffffffffu, bl, 0);
-                        bs = __shfl_sync(0xffffffffu, bs, 0);
-                        const unsigned below = (1u << lane) - 1u;
-                        if (lg) rays[bl + __popc(ml & below)] = rec;
-                        else if (keep) rays[RAYCAP8 - 1 - (bs + __popc(ms & below))] = rec;
-                    } else {
-                        const unsigned m = __ballot_sync(0xffffffffu, keep);
-                        int base = 0;
-                        if (lane == 0 && m) base = atomicAdd(&s_cnt[0], __popc(m));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (keep) rays[base + __popc(m & ((1u << lane) - 1u))] = rec;
+                    // long rays from the front of the list, short ones from the back
+                    const bool lg = keep && len >= LONG_RAY;
+                    const unsigned ml = __ballot_sync(0xffffffffu, lg);
+                    const unsigned ms = __ballot_sync(0xffffffffu, keep && !lg);
+                    int bl0 = 0, bs0 = 0;
+                    if (lane == 0) {
+                        if (ml) bl0 = atomicAdd(&s_cnt[0], __popc(ml));
+                        if (ms) bs0 = atomicAdd(&s_cnt[2], __popc(ms));
                     }
-                    c0 += NT;
+                    bl0 = __shfl_sync(0xffffffffu, bl0, 0);
+                    bs0 = __shfl_sync(0xffffffffu, bs0, 0);
+                    const unsigned below = (1u << lane) - 1u;
+                    if (lg) rays[bl0 + __popc(ml & below)] = rec;
+                    else if (keep) rays[C::RAYCAP - 1 - (bs0 + __popc(ms & below))] = rec;
+                    c0 += XT;
                     __syncthreads();
-                    if (s_cnt[0] + s_cnt[2] > RAYCAP8 - NT) break;
+                    if (s_cnt[0] + s_cnt[2] > C::RAYCAP - XT) break;
                 }
                 const int nl = s_cnt[0], nr = s_cnt[0] + s_cnt[2];
                 int k = 1, kc = 0;
@@ -698,27 +769,24 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
                         if (need) {
                             const int idx = base + __popc(m & ((1u << lane) - 1u));
                             if (idx < nr) {
-                                const RayRec8 rr = rays[idx < nl ? idx : RAYCAP8 - 1 - (idx - nl)];
+                                const RayRec8 rr = rays[idx < nl ? idx : C::RAYCAP - 1 - (idx - nl)];
                                 const int iu = (int)(rr.iuv & 0xffffu), iv = (int)(rr.iuv >> 16);
                                 Ray q;
-                                if (FX) {
-                                    ray_frame_outlined<PAR>(&A, &g, iu, iv, &q);
-                                } else {
-                                    float Ld;
-                                    ray_frame<PAR>(A, g, iu, iv, q, Ld);
-                                }
+                                float Ld;
+                                ray_frame<PAR>(A, g, iu, iv, q, Ld);
                                 gx = q.gx;
                                 gy = q.gy;
                                 gz = q.gz;
                                 sx = q.sx;
                                 sy = q.sy;
                                 sz = q.sz;
-                                const bool big = (rr.kk >> 31) != 0;
-                                ys = __ldg(pa + (size_t)iv * g.nu + iu) * (big ? scale : scale_f);
+                                const bool bigr = (rr.kk >> 31) != 0;
+                                const float yv = __ldg(pa + (size_t)iv * g.nu + iu);
+                                ys = ACC == ACC_SPLIT ? yv : yv * (bigr ? scale : scale_f);
                                 const int ka = (int)(rr.kk & 0xfffffu);
                                 k = ka - q.kr;
                                 kc = ka + (int)((rr.kk >> 20) & 0x7ffu) - q.kr;
-                                accc = big ? acc : acc_f;
+                                accc = (ACC == ACC_SPLIT || bigr) ? acc : acc + C::WORDS;
                             } else {
                                 live = false;
                             }
@@ -726,88 +794,217 @@ __device__ __forceinline__ void bp_matched_brick8(const float *__restrict__ pb, 
                     }
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
-                    if (FX) {
-                        const float kf = (float)k;
-                        scatter_sample_fx(accc, kf, gx, gy, gz, sx, sy, sz, ys, mox, moy, moz);
-                        scatter_sample_fx(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, mox, moy,
-                                          moz);
-                    } else {
-                        scatter_sample<false>(accc, k, gx, gy, gz, sx, sy, sz, ys, ox, oy, oz);
-                        scatter_sample<false>(accc, k + 1, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, ox, oy,
-                                              oz);
-                    }
+                    const float kf = (float)k;
+                    scatter_x<C, ACC>(accc, kf, gx, gy, gz, sx, sy, sz, ys, mox, moy, moz, scale, two_m);
+                    scatter_x<C, ACC>(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, mox, moy, moz,
+                                      scale, two_m);
                     k += 2;
                 }
                 __syncthreads();
             }
         }
+        // end of the angle: owned and rim sums to FP32 registers
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < OWNN; ++j) {
-            const int o = obase + (j / YR) * PP + (j % YR) * NW * PX;
-            const int v = (int)acc[o], vf = (int)acc_f[o];
-            acc[o] = 0u;
-            acc_f[o] = 0u;
-            const float add = fmaf((float)v, inv_scale, (float)vf * inv_scale_f);
-            if (OG) {
-                const int ix = x0 + lane, iy = y0 + warp + NW * (j % YR), iz = z0 + j / YR;
-                if (ix < g.nx && iy < g.ny && iz < g.nz) {
-                    float *dst = vb + ((size_t)iz * g.ny + iy) * g.nx + ix;
-                    *dst = (first ? 0.f : *dst) + add;
-                }
-            } else {
-                own[j] += add;
+        for (int j = 0; j < C::OWN; ++j)
+            own[j] += take_x<C>(acc, (j / YR + 1) * C::PP + (warp + NW * (j % YR) + 1) * C::PX + lane + 1, k1, k2);
+#pragma unroll
+        for (int j = 0; j < C::RIM_PER_THREAD; ++j) {
+            const int r = tid + j * XT;
+            if (r < C::NRIM) {
+                int lx, ly, lz;
+                C::rim_local(r, lx, ly, lz);
+                rimv[j] += take_x<C>(acc, lz * C::PP + ly * C::PX + lx, k1, k2);
             }
         }
-        first = false;
-        __syncthreads();
     }
-    double part = 0.0;
+    if (nonfinite) {
 #pragma unroll
-    for (int j = 0; j < OWNN; ++j) {
+        for (int j = 0; j < C::OWN; ++j) own[j] = __int_as_float(0x7fc00000);
+    }
+#pragma unroll
+    for (int j = 0; j < C::OWN; ++j) {
         const int ix = x0 + lane, iy = y0 + warp + NW * (j % YR), iz = z0 + j / YR;
-        const bool ok = ix < g.nx && iy < g.ny && iz < g.nz;
-        const size_t widx = ok ? ((size_t)iz * g.ny + iy) * g.nx + ix : 0;
-        float sum = OG ? (ok ? (first ? 0.f : vb[widx]) : 0.f) : own[OG ? 0 : j];
-        if (nonfinite) sum = __int_as_float(0x7fc00000);
-        if (MODE == BP_STORE_NORM) {
-            const float v = ep.scale * sum;
-            if (ok) {
-                vb[widx] = v;
-                part += (double)v * (double)v;
-            }
-        } else {
-            bp_epilogue<MODE>(sum, ok, widx, widx, ep, vb, 0);
+        if (ix < g.nx && iy < g.ny && iz < g.nz) sv[((size_t)iz * g.ny + iy) * g.nx + ix] = own[j];
+    }
+#pragma unroll
+    for (int j = 0; j < C::RIM_PER_THREAD; ++j) {
+        const int r = tid + j * XT;
+        if (r < C::NRIM) rb[r] = rimv[j];
+    }
+}
+
+// Brick (bl % nbx, ...) of batch item blockIdx.y: owned sums (unscaled) to
+// sumv, rim sums to rim[(item * nbricks + brick) * NRIM + r].
+template <class C, int ACC, bool PAR>
+__global__ void __launch_bounds__(C::XT, C::MINB)
+    k_bp_mx(const float *__restrict__ proj, float *__restrict__ sumv, float *__restrict__ rim,
+            const Angle *__restrict__ angles, Grid g, const unsigned int *__restrict__ absmax, int nbx, int nby,
+            int nbricks) {
+    const int b = blockIdx.y, bl = blockIdx.x;
+    mx_brick<C, ACC, PAR>(proj + (size_t)b * g.nA * g.nv * g.nu, sumv + (size_t)b * g.nx * g.ny * g.nz,
+                          rim + ((size_t)b * nbricks + bl) * C::NRIM, angles, g, __uint_as_float(absmax[b]), bl % nbx,
+                          (bl / nbx) % nby, bl / (nbx * nby));
+}
+
+// Volumes of different sizes and geometries in one launch (packed back to
+// back, at most MXR_MAXV): blocks blk0[v] .. blk0[v + 1] - 1 are volume v's
+// bricks, its rim sums start at rim + r0[v], its voxels at v0[v] of sumv and
+// of the output (voxels vox0[v] .. vox0[v + 1] - 1 of the merge).
+constexpr int MXR_MAXV = 16;
+struct MxRagged {
+    int nvol;
+    int blk0[MXR_MAXV + 1];
+    int nbx[MXR_MAXV], nby[MXR_MAXV];
+    int a0[MXR_MAXV];
+    long long p0[MXR_MAXV], v0[MXR_MAXV + 1], r0[MXR_MAXV];
+    float scale[MXR_MAXV];
+    Grid g[MXR_MAXV];
+};
+
+__device__ __forceinline__ int ragged_slot(const int *first, int n, long long key) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= key) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class C, int ACC, bool PAR>
+__global__ void __launch_bounds__(C::XT, C::MINB)
+    k_bp_mx_ragged(const float *__restrict__ proj, float *__restrict__ sumv, float *__restrict__ rim,
+                   const Angle *__restrict__ angles, const __grid_constant__ MxRagged tab,
+                   const unsigned int *__restrict__ absmax) {
+    const int v = ragged_slot(tab.blk0, tab.nvol, blockIdx.x);
+    const int bl = blockIdx.x - tab.blk0[v], nbx = tab.nbx[v], nby = tab.nby[v];
+    mx_brick<C, ACC, PAR>(proj + tab.p0[v], sumv + tab.v0[v], rim + tab.r0[v] + (size_t)bl * C::NRIM,
+                          angles + tab.a0[v], tab.g[v], __uint_as_float(absmax[v]), bl % nbx, (bl / nbx) % nby,
+                          bl / (nbx * nby));
+}
+
+// Owner sum of voxel i of a volume plus the rims of its up to seven lower
+// neighbour bricks, in a fixed order.
+template <class C>
+__device__ __forceinline__ float mx_gather(const float *__restrict__ sv, const float *__restrict__ rb, const Grid &g,
+                                           int nbx, int nby, size_t i) {
+    const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((size_t)g.nx * g.ny));
+    const int bx = ix / C::XB, by = iy / C::YB, bz = iz / C::ZB;
+    const int lx = ix - bx * C::XB + 1, ly = iy - by * C::YB + 1, lz = iz - bz * C::ZB + 1;
+    float sum = sv[i];
+#pragma unroll
+    for (int m = 1; m < 8; ++m) {
+        const int dx = m & 1, dy = (m >> 1) & 1, dz = (m >> 2) & 1;
+        if ((dx && (lx != 1 || bx == 0)) || (dy && (ly != 1 || by == 0)) || (dz && (lz != 1 || bz == 0))) continue;
+        const int nb = ((bz - dz) * nby + (by - dy)) * nbx + (bx - dx);
+        sum += rb[(size_t)nb * C::NRIM + C::rim_index(lx + dx * C::XB, ly + dy * C::YB, lz + dz * C::ZB)];
+    }
+    return sum;
+}
+
+// The ragged merge: voxel i of the packed volumes (one thread each), the
+// epilogue with volume v's output multiplier.
+template <class C, int MODE>
+__global__ void __launch_bounds__(256) k_bp_mx_merge_ragged(const float *__restrict__ sumv,
+                                                            const float *__restrict__ rim, float *__restrict__ vol,
+                                                            const __grid_constant__ MxRagged tab, BpEpilogue ep) {
+    const long long n = tab.v0[tab.nvol];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int lo = 0, hi = tab.nvol - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab.v0[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int v = lo;
+        const size_t local = (size_t)(i - tab.v0[v]);
+        const float sum = mx_gather<C>(sumv + tab.v0[v], rim + tab.r0[v], tab.g[v], tab.nbx[v], tab.nby[v], local);
+        BpEpilogue e = ep;
+        e.scale = tab.scale[v];
+        bp_epilogue<MODE>(sum, true, (size_t)i, local, e, vol, 0);
+    }
+}
+
+// Owner sum + the rims of the up to seven lower neighbours (fixed order),
+// then the epilogue of the mode; one thread per voxel.
+template <class C, int MODE>
+__global__ void __launch_bounds__(256) k_bp_mx_merge(const float *__restrict__ sumv, const float *__restrict__ rim,
+                                                     float *__restrict__ vol, Grid g, BpEpilogue ep, int nbx,
+                                                     int nby, int nbricks) {
+    const int b = blockIdx.y;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t rounds = (n + stride - 1) / stride;  // every thread the same count (BP_STORE_NORM reduces per block)
+    for (size_t rd = 0; rd < rounds; ++rd) {
+        const size_t i = rd * stride + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const bool ok = i < n;
+        const float sum = ok ? mx_gather<C>(sumv + (size_t)b * n, rim + (size_t)b * nbricks * C::NRIM, g, nbx, nby, i)
+                             : 0.f;
+        bp_epilogue<MODE>(sum, ok, (size_t)b * n + (ok ? i : 0), ok ? i : 0, ep, vol, b);
+    }
+}
+
+template <class C, int ACC>
+cudaError_t launch_mx(const Grid &g, const Angle *d_angles, const float *proj, float *vol, int batch, int mode,
+                      const BpEpilogue &ep, cudaStream_t s) {
+    const int nbx = (g.nx + C::XB - 1) / C::XB, nby = (g.ny + C::YB - 1) / C::YB, nbz = (g.nz + C::ZB - 1) / C::ZB;
+    const int nbricks = nbx * nby * nbz;
+    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    const bool in_place = mode == BP_STORE || mode == BP_STORE_NORM;  // the output holds the owned sums
+    float *rim = nullptr, *sumv = nullptr;
+    cudaError_t e = cudaMallocAsync(&rim, sizeof(float) * C::NRIM * (size_t)nbricks * batch, s);
+    if (e == cudaSuccess && !in_place) e = cudaMallocAsync(&sumv, sizeof(float) * nvox * batch, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (rim) cudaFreeAsync(rim, s);
+        return cudaErrorMemoryAllocation;
+    }
+    if (in_place) sumv = vol;
+    KernelTimer kt(ACC == ACC_SPLIT ? TG_KT_BP_MATCHED_SPLIT : TG_KT_BP_MATCHED, s);  // bricks and merge
+    {
+        auto kern = g.parallel ? k_bp_mx<C, ACC, true> : k_bp_mx<C, ACC, false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e == cudaSuccess) {
+            kern<<<dim3((unsigned)nbricks, batch), C::XT, C::SMEM, s>>>(proj, sumv, rim, d_angles, g, ep.absmax, nbx,
+                                                                        nby, nbricks);
+            count_launch();
+            e = cudaGetLastError();
         }
     }
-    if (MODE == BP_STORE_NORM) block_add_bp(part, ep.norm);
+    if (e == cudaSuccess) {
+        size_t nb = (nvox + 255) / 256;
+        if (nb > 152 * 16) nb = 152 * 16;
+        dim3 grid((unsigned)nb, batch);
+        switch (mode) {
+            case BP_STORE:
+                k_bp_mx_merge<C, BP_STORE><<<grid, 256, 0, s>>>(sumv, rim, vol, g, ep, nbx, nby, nbricks);
+                break;
+            case BP_SIRT:
+                k_bp_mx_merge<C, BP_SIRT><<<grid, 256, 0, s>>>(sumv, rim, vol, g, ep, nbx, nby, nbricks);
+                break;
+            case BP_STORE_NORM:
+                k_bp_mx_merge<C, BP_STORE_NORM><<<grid, 256, 0, s>>>(sumv, rim, vol, g, ep, nbx, nby, nbricks);
+                break;
+            case BP_MLEM:
+                k_bp_mx_merge<C, BP_MLEM><<<grid, 256, 0, s>>>(sumv, rim, vol, g, ep, nbx, nby, nbricks);
+                break;
+            default: e = cudaErrorInvalidValue;
+        }
+        if (e == cudaSuccess) {
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    cudaFreeAsync(rim, s);
+    if (!in_place) cudaFreeAsync(sumv, s);
+    return e;
 }
 
-template <int MODE, bool PAR, int NT, bool OG, bool LF, bool FX>
-__global__ void __launch_bounds__(NT, 1)
-    k_bp_matched8(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
-                  BpEpilogue ep, int nbx, int nby) {
-    const int bl = blockIdx.x, b = blockIdx.y;
-    BpEpilogue e = ep;
-    if (e.norm) e.norm += b;
-    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-    bp_matched_brick8<MODE, PAR, NT, OG, LF, FX>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
-                                             __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby,
-                                             bl / (nbx * nby));
-}
-
-template <int MODE, bool F32, bool PAR, bool I64 = false>
-__global__ void __launch_bounds__(MT, 1)
-    k_bp_matched(const float *__restrict__ proj, float *__restrict__ vol, const Angle *__restrict__ angles, Grid g,
-                 BpEpilogue ep, int nbx, int nby) {
-    const int bl = blockIdx.x, b = blockIdx.y;
-    BpEpilogue e = ep;
-    if (e.norm) e.norm += b;
-    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-    bp_matched_brick<MODE, F32, PAR, I64>(proj + (size_t)b * g.nA * g.nv * g.nu, vol + b * nvox, angles, g, e,
-                                          __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby,
-                                          bl / (nbx * nby));
-}
+// One 1024-thread CTA per SM (measured faster than two 512-thread CTAs on
+// 32x16x16 bricks: 3.09 s against 3.28 s for the 512^3 / 720-view scan).
+using MxA = Mx<32, 32, 16, 1024, 2048>;
 
 // Volumes of different sizes and geometries in one launch (packed back to
 // back): blocks blk0[v] .. blk0[v + 1] - 1 are volume v's bricks.
@@ -918,57 +1115,14 @@ __global__ void __launch_bounds__(256) k_bp_fdk(const float *__restrict__ proj, 
     }
 }
 
-template <int MODE, bool F32, bool PAR, bool I64 = false>
+template <int MODE, bool F32, bool PAR>
 cudaError_t launch_matched_t(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
                              const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    auto kern = k_bp_matched<MODE, F32, PAR, I64>;
+    auto kern = k_bp_matched<MODE, F32, PAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MATCHED_SMEM);
     if (e != cudaSuccess) return e;
     kern<<<grid, MT, MATCHED_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
     return cudaSuccess;
-}
-
-// 64-bit fixed point in place of FP32 accumulation (experiment switch TG_BP_I64)
-template <int MODE>
-cudaError_t launch_matched_i64(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
-                               const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    return g.parallel ? launch_matched_t<MODE, false, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
-                      : launch_matched_t<MODE, false, false, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-}
-
-template <int MODE, int NT, bool OG, bool LF, bool FX = false>
-cudaError_t launch_matched8_t(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
-                              const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    auto kern = k_bp_matched8<MODE, false, NT, OG, LF, FX>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MATCHED8_SMEM);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, NT, MATCHED8_SMEM, s>>>(proj, vol, d_angles, g, ep, nbx, nby);
-    return cudaSuccess;
-}
-
-// Compact-record kernels (experiment selection by TG_BP_IMPL); returns
-// cudaErrorNotSupported when the request stays with k_bp_matched.
-template <int MODE>
-cudaError_t launch_matched8(dim3 grid, const float *proj, float *vol, const Angle *d_angles, const Grid &g,
-                            const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
-    const char *impl = getenv("TG_BP_IMPL");
-    if (!impl || g.parallel || ep.fp32_acc) return cudaErrorNotSupported;
-    const double dmin = fmin(fmin(g.dx, g.dy), g.dz);
-    const double chord = sqrt((double)(RX * RX) * g.dx * g.dx + (double)(RY * RY) * g.dy * g.dy +
-                              (double)(RZ * RZ) * g.dz * g.dz) / (double)g.delta + 2.0;
-    if (!(g.kmax < 1048000.f) || !(chord < 2000.0) || dmin <= 0.0) return cudaErrorNotSupported;
-    const std::string v(impl);
-    if (v == "c512") return launch_matched8_t<MODE, 512, false, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "c512lf") return launch_matched8_t<MODE, 512, false, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "c1024") return launch_matched8_t<MODE, 1024, false, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "c1024lf") return launch_matched8_t<MODE, 1024, false, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "g512lf") return launch_matched8_t<MODE, 512, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "g1024") return launch_matched8_t<MODE, 1024, true, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "g1024lf") return launch_matched8_t<MODE, 1024, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "x512lf") return launch_matched8_t<MODE, 512, false, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "x1024lf") return launch_matched8_t<MODE, 1024, false, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    if (v == "xg1024lf") return launch_matched8_t<MODE, 1024, true, true, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-    return cudaErrorNotSupported;
 }
 
 template <int MODE, bool F32>
@@ -976,6 +1130,80 @@ cudaError_t launch_matched(dim3 grid, const float *proj, float *vol, const Angle
                            const BpEpilogue &ep, int nbx, int nby, cudaStream_t s) {
     return g.parallel ? launch_matched_t<MODE, F32, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
                       : launch_matched_t<MODE, F32, false>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
+}
+
+// The compact records of the exclusive-cell bricks hold a sample index
+// below 2^20, a ray's run in a brick below 2^11 samples and 16-bit pixel
+// indices.
+bool mx_fits(const Grid &g) {
+    const double chord = sqrt((double)(MxA::XA * MxA::XA) * g.dx * g.dx + (double)(MxA::YA * MxA::YA) * g.dy * g.dy +
+                              (double)(MxA::ZA * MxA::ZA) * g.dz * g.dz) / (double)g.delta + 2.0;
+    return g.kmax < 1048000.f && chord < 2000.0 && g.nu <= 65535 && g.nv <= 65535;
+}
+
+// Ragged exclusive-cell backprojection of n <= MXR_MAXV volumes (32-bit
+// fixed point): ep.absmax[v] already holds each volume's max |y|.
+cudaError_t launch_mx_ragged(const Grid *gs, const float *scales, int n, const int *angle0, const Angle *d_angles,
+                             const float *proj, float *vol, int mode, const BpEpilogue &ep, cudaStream_t s) {
+    using C = MxA;
+    MxRagged tab;
+    memset(&tab, 0, sizeof(tab));
+    tab.nvol = n;
+    long long blocks = 0, rims = 0, pix = 0, vox = 0;
+    for (int k = 0; k < n; ++k) {
+        const Grid &g = gs[k];
+        const int nbx = (g.nx + C::XB - 1) / C::XB, nby = (g.ny + C::YB - 1) / C::YB, nbz = (g.nz + C::ZB - 1) / C::ZB;
+        tab.g[k] = g;
+        tab.nbx[k] = nbx;
+        tab.nby[k] = nby;
+        tab.a0[k] = angle0[k];
+        tab.p0[k] = pix;
+        tab.v0[k] = vox;
+        tab.r0[k] = rims;
+        tab.scale[k] = scales[k];
+        tab.blk0[k] = (int)blocks;
+        blocks += (long long)nbx * nby * nbz;
+        rims += (long long)nbx * nby * nbz * C::NRIM;
+        pix += (long long)g.nA * g.nv * g.nu;
+        vox += (long long)g.nx * g.ny * g.nz;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    }
+    tab.blk0[n] = (int)blocks;
+    tab.v0[n] = vox;
+    if (blocks == 0) return cudaSuccess;
+    const bool in_place = mode == BP_STORE;
+    float *rim = nullptr, *sumv = nullptr;
+    cudaError_t e = cudaMallocAsync(&rim, sizeof(float) * (size_t)rims, s);
+    if (e == cudaSuccess && !in_place) e = cudaMallocAsync(&sumv, sizeof(float) * (size_t)vox, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (rim) cudaFreeAsync(rim, s);
+        return cudaErrorMemoryAllocation;
+    }
+    if (in_place) sumv = vol;
+    {
+        KernelTimer kt(TG_KT_BP_MATCHED, s);
+        auto kern = gs[0].parallel ? k_bp_mx_ragged<C, ACC_FIX, true> : k_bp_mx_ragged<C, ACC_FIX, false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e == cudaSuccess) {
+            kern<<<(unsigned)blocks, C::XT, C::SMEM, s>>>(proj, sumv, rim, d_angles, tab, ep.absmax);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            long long nb = (vox + 255) / 256;
+            if (nb > 152 * 16) nb = 152 * 16;
+            if (mode == BP_STORE)
+                k_bp_mx_merge_ragged<C, BP_STORE><<<(unsigned)nb, 256, 0, s>>>(sumv, rim, vol, tab, ep);
+            else
+                k_bp_mx_merge_ragged<C, BP_SIRT><<<(unsigned)nb, 256, 0, s>>>(sumv, rim, vol, tab, ep);
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    cudaFreeAsync(rim, s);
+    if (!in_place) cudaFreeAsync(sumv, s);
+    return e;
 }
 
 }  // namespace
@@ -998,24 +1226,14 @@ cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles,
         }
         dim3 grid((unsigned)(nbx * nby * nbz), batch);
         const bool f32 = ep.fp32_acc != 0;
+        // The exclusive-cell bricks (k_bp_mx) unless the call must not allocate
+        // (their rim buffer is scratch) or a sample index or a ray's run in a
+        // brick exceeds the compact record (2^20 and 2^11 samples).
+        if (!ep.noalloc && mx_fits(g)) {
+            return (f32 || mode == BP_MLEM) ? launch_mx<MxA, ACC_SPLIT>(g, d_angles, proj, vol, batch, mode, ep, s)
+                                            : launch_mx<MxA, ACC_FIX>(g, d_angles, proj, vol, batch, mode, ep, s);
+        }
         KernelTimer kt(TG_KT_BP_MATCHED, s);
-        if (f32 && getenv("TG_BP_I64") && (mode == BP_STORE || mode == BP_SIRT || mode == BP_MLEM)) {
-            e = mode == BP_STORE ? launch_matched_i64<BP_STORE>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
-                : mode == BP_SIRT ? launch_matched_i64<BP_SIRT>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
-                                  : launch_matched_i64<BP_MLEM>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-            if (e != cudaSuccess) return e;
-            count_launch();
-            return cudaGetLastError();
-        }
-        if (mode == BP_STORE || mode == BP_STORE_NORM) {
-            e = mode == BP_STORE ? launch_matched8<BP_STORE>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
-                                 : launch_matched8<BP_STORE_NORM>(grid, proj, vol, d_angles, g, ep, nbx, nby, s);
-            if (e == cudaSuccess) {
-                count_launch();
-                return cudaGetLastError();
-            }
-            if (e != cudaErrorNotSupported) return e;
-        }
         switch (mode) {
             case BP_STORE:
                 e = f32 ? launch_matched<BP_STORE, true>(grid, proj, vol, d_angles, g, ep, nbx, nby, s)
@@ -1090,9 +1308,11 @@ cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int n
         tab.nvol = n;
         long long blocks = 0, nmax = 0;
         size_t cvox = 0, cpix = 0;
+        bool mx_ok_all = true;
         for (int k = 0; k < n; ++k) {
             const Grid &g = gs[v0 + k];
             if (!(g.wbound > 0.f)) return cudaErrorInvalidValue;
+            mx_ok_all = mx_ok_all && mx_fits(g);
             if (g.parallel != gs[0].parallel) return cudaErrorInvalidValue;  // one beam mode per call
             const int nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY, nbz = (g.nz + BZ - 1) / BZ;
             tab.g[k] = g;
@@ -1119,6 +1339,13 @@ cudaError_t launch_backproject_ragged(const Grid *gs, const float *scales, int n
             if (nb > 152 * 4) nb = 152 * 4;
             k_absmax_ragged<<<dim3((unsigned)nb, n), 256, 0, s>>>(proj + pix, at, ep.absmax);
             count_launch();
+        }
+        if (mx_ok_all && !ep.noalloc && (mode == BP_STORE || mode == BP_SIRT)) {
+            e = launch_mx_ragged(gs + v0, scales + v0, n, angle0 + v0, d_angles, proj + pix, vol + vox, mode, ep, s);
+            if (e != cudaSuccess) return e;
+            vox += cvox;
+            pix += cpix;
+            continue;
         }
         if (blocks > 0) {
 #define TG_BPR(M, F, P)                                                                                           \

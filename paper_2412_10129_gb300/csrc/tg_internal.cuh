@@ -126,6 +126,7 @@ struct BpEpilogue {
     unsigned int *absmax;  // device scratch words (TG_MATCHED: max |y| per batch item)
     int fp32_acc;          // TG_MATCHED: accumulate in FP32 (per-voxel relative precision)
     float *acc;            // TG_SIDDON_BP, modes other than BP_STORE: device scratch of the volume's size
+    int noalloc;           // the launcher must not allocate scratch (tg_backproject_noalloc)
 };
 
 // Host helpers (tg_geometry.cu).
@@ -226,6 +227,11 @@ cudaError_t launch_lg_update(const float *x, const float *net, float *xn, size_t
 
 // Vector kernels (tg_vector.cu).
 cudaError_t launch_safe_inverse(float *a, size_t n, cudaStream_t s);
+// Column weights: 1 / a where a >= floor, else 0.  floor = coverage_floor(g):
+// a voxel whose backprojected ones fall below 1e-3 of one full-weight
+// sample (1e-3 delta) counts as unseen by the block.
+cudaError_t launch_column_inverse(float *a, size_t n, float floor, cudaStream_t s);
+inline float coverage_floor(const Grid &g) { return 1e-3f * g.delta; }
 cudaError_t launch_fill(float *a, float v, size_t n, cudaStream_t s);
 cudaError_t launch_sub(const float *a, const float *b, float *out, size_t n, cudaStream_t s);
 cudaError_t launch_norm2(const float *a, size_t n, double *acc, cudaStream_t s);

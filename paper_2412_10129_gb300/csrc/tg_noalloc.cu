@@ -132,6 +132,7 @@ extern "C" tg_status tg_backproject_noalloc(const tg_geometry *geo, const double
     BpEpilogue ep{};
     ep.scale = method == TG_MATCHED ? g.delta : method == TG_SIDDON_BP ? 1.f : (float)(M_PI / nAngles);
     ep.absmax = amax;  // zeroed by the launcher before use
+    ep.noalloc = 1;
     e = launch_backproject(method, g, dA, proj, vol, batch, BP_STORE, ep, s);
     if (e == cudaErrorMemoryAllocation) return TG_ERR_OOM;
     return e == cudaSuccess ? TG_OK : TG_ERR_CUDA;

@@ -40,6 +40,15 @@ __global__ void k_safe_inverse(float *a, size_t n) {
     }
 }
 
+// 1 / a where a >= floor, else 0 (the column weights of the Kaczmarz-type
+// and EM methods: a voxel covered by less than `floor` counts as unseen).
+__global__ void k_column_inverse(float *a, size_t n, float floor) {
+    for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) {
+        const float v = a[i];
+        a[i] = v >= floor ? 1.f / v : 0.f;
+    }
+}
+
 __global__ void k_fill(float *a, float v, size_t n) {
     for (size_t i = blockIdx.x * (size_t)TPB + threadIdx.x; i < n; i += (size_t)gridDim.x * TPB) a[i] = v;
 }
@@ -280,6 +289,13 @@ __global__ void k_pocs_control(const double *sc, float *dtvg, int phase, int fir
 cudaError_t launch_safe_inverse(float *a, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_safe_inverse<<<blocks_for(n), TPB, 0, s>>>(a, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column_inverse(float *a, size_t n, float floor, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_column_inverse<<<blocks_for(n), TPB, 0, s>>>(a, n, floor);
     count_launch();
     return cudaGetLastError();
 }

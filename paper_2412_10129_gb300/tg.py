@@ -544,7 +544,8 @@ def test_conv_wait(stall: bool, budget_cycles: int = 0) -> None:
     _check("tg_test_conv_wait", load().tg_test_conv_wait(1 if stall else 0, int(budget_cycles)))
 
 
-KERNEL_CLASSES = {"fp_interp": 0, "fp_siddon": 1, "bp_matched": 2, "bp_fdk": 3, "bp_siddon": 4, "fdk_filter": 5}
+KERNEL_CLASSES = {"fp_interp": 0, "fp_siddon": 1, "bp_matched": 2, "bp_fdk": 3, "bp_siddon": 4, "fdk_filter": 5,
+                  "bp_matched_split": 6}
 
 
 def kernel_timing(enable: bool) -> None:

@@ -63,16 +63,40 @@ def test_cgls_exact_data_and_warm_start(problem):
     assert hist.max() < 1e-10
 
 
-def dense_sirt(A, b, niter, lam=1.0, nonneg=True, x0=None):
+def dense_sirt(A, b, niter, lam=1.0, nonneg=True, x0=None, floor=0.0):
+    """SIRT on a materialised A; a column whose sum is below `floor` (the
+    coverage reading: less than 1e-3 of one full-weight sample) gets V = 0."""
     rs, cs = A.sum(1), A.sum(0)
     W = np.where(rs != 0, 1.0 / np.where(rs != 0, rs, 1), 0.0)
-    V = np.where(cs != 0, 1.0 / np.where(cs != 0, cs, 1), 0.0)
+    seen = (cs != 0) & (cs >= floor)
+    V = np.where(seen, 1.0 / np.where(seen, cs, 1), 0.0)
     x = np.zeros(A.shape[1]) if x0 is None else x0.copy()
     for _ in range(niter):
         x = x + lam * V * (A.T @ (W * (b - A @ x)))
         if nonneg:
             x = np.maximum(x, 0)
     return x
+
+
+def test_coverage_floor_drops_thin_columns(problem, monkeypatch):
+    """V = 0 for a voxel whose column sum is below the coverage floor
+    (1e-3 of one sample step by default); raised to the 30th percentile of
+    the column sums, the floor removes the thinner columns, and SIRT still
+    equals the dense iteration written with the same rule."""
+    g, A, _, b = problem
+    delta = 0.5 * min(g.dVoxel)
+    assert oracle.coverage_floor(g) == pytest.approx(1e-3 * delta, rel=1e-15)
+    cs = A.sum(0)
+    frac = np.percentile(cs[cs > 0], 30) / delta
+    monkeypatch.setattr(oracle, "COVERAGE_MIN", frac)
+    floor = frac * delta
+    thin = (cs > 0) & (cs < floor)
+    assert thin.sum() > 0
+    _, V = oracle.sirt_weights(g)
+    assert np.all(V.reshape(-1)[thin] == 0.0)
+    np.testing.assert_allclose(V.reshape(-1)[cs >= floor], 1.0 / cs[cs >= floor], rtol=1e-10)
+    x, _ = oracle.sirt(g, b.reshape(g.proj_shape), 3)
+    np.testing.assert_allclose(x.reshape(-1), dense_sirt(A, b, 3, floor=floor), rtol=1e-10, atol=1e-12)
 
 
 def test_sirt_matches_dense_iteration(problem):
