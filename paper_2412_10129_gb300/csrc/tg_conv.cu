@@ -583,6 +583,10 @@ cudaError_t launch_conv3d_wgrad(const void *x, const void *gy, float *dw, int N,
         cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * 27 * cin * cout, s);
         if (e != cudaSuccess) return e;
     }
+    const char *env = getenv("TG_CONV_IMPL");
+    if (!(env && strcmp(env, "mma") == 0) && ((((uintptr_t)x | (uintptr_t)gy) & 15u) == 0) &&
+        wgrad_tc_supported(cin, cout, X))
+        return launch_conv3d_wgrad_tc(x, gy, dw, N, Z, Y, X, cin, cout, s);
     if (cin == 16 && cout == 32) return run_wgrad_mma<16, 32>(x, gy, dw, N, Z, Y, X, s);
     if (cin == 32 && cout == 32) return run_wgrad_mma<32, 32>(x, gy, dw, N, Z, Y, X, s);
     if (cin == 32 && cout == 8) return run_wgrad_mma<32, 8>(x, gy, dw, N, Z, Y, X, s);

@@ -474,6 +474,206 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3d_tc(const float *__rest
     if (tid == 0 && s_err) atomicExch(&g_tc_error, 1);
 }
 
+// ---- weight gradient ---------------------------------------------------------
+//
+// dW[dz][dy][dx][o][c] = sum_v gy[v][o] x[v + (dz - 1, dy - 1, dx - 1)][c]
+// is a contraction over the voxels (K) with both output dimensions channels.
+// A work item is the 64 voxels x0 .. x0 + 63 of one (n, z, y) row; for it
+// the producer stages by TMA (zero fill outside the volume)
+//   A: gy of the rows z - 1, z, z + 1 (slots a = 0, 1, 2; slot 3 stays zero),
+//      M = 4 x 32 = 128,
+//   B: x of the rows (z, y + ey) shifted by ex voxels, the nine (ey, ex) as
+//      slots j = 3 (ey + 1) + (ex + 1), N = 9 CIN,
+// both as the tensors store them, channel-contiguous: MN-major operands in
+// which a voxel is one K row of 64 (or 32) bytes, eight rows form a swizzle
+// atom, atoms of one slot follow each other along K (the descriptor's stride
+// byte offset) and the slots follow each other along M or N (its leading
+// byte offset).  Over all items,
+//     D[32 a + o][CIN j + c] = sum_u gy[u + (a - 1, 0, 0)][o] x[u + (0, ey, ex)][c]
+// is dW at the offset (1 - a, ey, ex): substituting v = u + (a - 1, 0, 0),
+// every term that the item ranges leave out has a zero factor (the
+// convolution's zero padding).  D stays in tensor memory over all of a CTA's
+// items (4 x 64 voxels x 128 x 9 CIN MACs per item, in two MMAs of N = 160 and
+// 128 for CIN = 32, one of N = 144 for CIN = 16); at the end warps 2-5 read it
+// back and add it to dw, one FP32 atomic per weight and CTA.  Three of the
+// four A slots carry data, so a quarter of the tensor-core work multiplies
+// zeros: 27 offsets do not split into products of 4 x 9 slots.
+constexpr int WG_K = 64;  // voxels per item (MMA K per stage)
+constexpr int WG_THREADS = 192;
+
+struct WgParams {
+    CUtensorMap mx, mg;
+    int Z, Y, nxc, items;
+};
+
+template <int CIN>
+struct WgShape {
+    static constexpr int AROW = 64;                   // bytes of a gradient voxel (32 channels)
+    static constexpr int BROW = 2 * CIN;              // bytes of an input voxel
+    static constexpr int ASLOT = WG_K * AROW;
+    static constexpr int BSLOT = WG_K * BROW;
+    static constexpr int STAGE = 4 * ASLOT + 9 * BSLOT;
+    static constexpr int STAGES = CIN == 32 ? 4 : 6;
+    static constexpr unsigned TX = 3 * ASLOT + 9 * BSLOT;  // bytes landing per item
+    static constexpr unsigned BLAYOUT = CIN == 32 ? 4u : 6u;  // 64- or 32-byte swizzle
+    static constexpr int N1 = CIN == 32 ? 160 : 144;  // slots 0-4 (0-8)
+    static constexpr int N2 = CIN == 32 ? 128 : 0;    // slots 5-8
+    static constexpr int TCOLS = CIN == 32 ? 512 : 256;
+    static constexpr int NBAR = 2 * STAGES + 1;
+    static constexpr int GUARD = 2048;
+    static constexpr int SMEM = 1024 + STAGES * STAGE + NBAR * 8 + GUARD;
+    static_assert(STAGE % 1024 == 0 && SMEM <= 232448, "stage layout");
+    // kind::f16, D = F32, A = B = BF16, both MN-major, M = 128
+    static constexpr unsigned IDESC0 =
+        (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((unsigned)(128 >> 4) << 24);
+    static constexpr unsigned IDESC1 = IDESC0 | ((unsigned)(N1 >> 3) << 17);
+    static constexpr unsigned IDESC2 = IDESC0 | ((unsigned)(N2 >> 3) << 17);
+};
+
+template <int CIN>
+__global__ void __launch_bounds__(WG_THREADS, 1) k_conv3d_wgrad_tc(float *__restrict__ dw,
+                                                                   const __grid_constant__ WgParams p) {
+    using S = WgShape<CIN>;
+    extern __shared__ unsigned char wg_smem_raw[];
+    __shared__ unsigned s_tmem;
+    __shared__ int s_err;
+    __shared__ int s_progress;
+    const unsigned raw = smem_u32(wg_smem_raw);
+    const unsigned base = (raw + 1023u) & ~1023u;
+    const unsigned st0 = base;
+    const unsigned bar0 = base + S::STAGES * S::STAGE;
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 8u * (S::STAGES + s); };
+    const unsigned done = bar0 + 8u * (2 * S::STAGES);
+    const long long budget = g_tc_wait_cycles;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int *err = &s_err;
+    volatile int *progress = &s_progress;
+
+    if (tid == 0) {
+        s_err = 0;
+        s_progress = 0;
+        for (int s = 0; s < S::STAGES; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // A slot 3 of every stage: zeros, never loaded
+    for (int i = tid; i < S::STAGES * (S::ASLOT / 16); i += WG_THREADS) {
+        const int s = i / (S::ASLOT / 16), e = i % (S::ASLOT / 16);
+        *reinterpret_cast<uint4 *>(wg_smem_raw + (base - raw) + s * S::STAGE + 3 * S::ASLOT + 16 * e) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"((unsigned)S::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int q = 0;
+            for (int it = blockIdx.x; it < p.items; it += gridDim.x, ++q) {
+                const int s = q % S::STAGES;
+                if (!mbar_wait(empty(s), ((q / S::STAGES) & 1) ^ 1, err, budget)) break;
+                const int xc = it % p.nxc, row = it / p.nxc;
+                const int y = row % p.Y, zn = row / p.Y, z = zn % p.Z, n = zn / p.Z, x0 = xc * WG_K;
+                mbar_expect_tx(full(s), S::TX);
+                const unsigned sa = st0 + s * S::STAGE, sb = sa + 4 * S::ASLOT;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) tma_load_5d(sa + a * S::ASLOT, &p.mg, full(s), 0, x0, y, z + a - 1, n);
+#pragma unroll
+                for (int j = 0; j < 9; ++j)
+                    tma_load_5d(sb + j * S::BSLOT, &p.mx, full(s), 0, x0 + j % 3 - 1, y + j / 3 - 1, z, n);
+            }
+            // every stage's last fill has landed before the CTA exits
+            for (int qq = q > S::STAGES ? q - S::STAGES : 0; qq < q; ++qq)
+                mbar_drain(full(qq % S::STAGES), (qq / S::STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int q = 0;
+            for (int it = blockIdx.x; it < p.items; it += gridDim.x, ++q) {
+                const int s = q % S::STAGES;
+                if (!mbar_wait(full(s), (q / S::STAGES) & 1, err, budget)) break;
+                *progress = q + 1;
+                tc_fence_after();
+                const unsigned sa = st0 + s * S::STAGE, sb = sa + 4 * S::ASLOT;
+#pragma unroll
+                for (int kk = 0; kk < WG_K / 16; ++kk) {
+                    const unsigned acc = (q | kk) != 0;
+                    const unsigned long long a = sdesc(sa + kk * 16 * S::AROW, S::ASLOT, 8 * S::AROW, 4u);
+                    tc_mma(tmem, a, sdesc(sb + kk * 16 * S::BROW, S::BSLOT, 8 * S::BROW, S::BLAYOUT),
+                           S::IDESC1, acc);
+                    if (S::N2)
+                        tc_mma(tmem + S::N1, a,
+                               sdesc(sb + 5 * S::BSLOT + kk * 16 * S::BROW, S::BSLOT, 8 * S::BROW, S::BLAYOUT),
+                               S::IDESC2, acc);
+                }
+                tc_commit(empty(s));
+            }
+            // all MMAs of this thread have completed before tensor memory is read or freed
+            tc_commit(done);
+            mbar_drain(done, 0);
+        }
+    } else {  // epilogue: warps 2..5, accumulator lanes 32 (warp % 4) ..
+        const int a = warp & 3;
+        int ok = 0;
+        if (lane == 0) {
+            // the wait restarts its budget whenever the MMA issuer takes a
+            // further item, so that long launches do not time out
+            long long t0 = clock64();
+            int last = 0;
+            while (true) {
+                if (mbar_try(done, 0)) {
+                    ok = *err ? 0 : 1;
+                    break;
+                }
+                if (*err) break;
+                const int pr = *progress;
+                if (pr != last) {
+                    last = pr;
+                    t0 = clock64();
+                } else if (clock64() - t0 > budget) {
+                    *err = 1;
+                    break;
+                }
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok && a < 3) {
+            tc_fence_after();
+            const int o = lane, dz = 2 - a;
+#pragma unroll 1
+            for (int j = 0; j < 9; ++j) {
+                float v[32];
+                const unsigned ta = tmem + ((unsigned)(32 * a) << 16) + (unsigned)(j * CIN);
+                if (CIN == 32) tc_ld32(ta, v);
+                else tc_ld16(ta, v);
+                float *d = dw + ((size_t)((dz * 3 + j / 3) * 3 + j % 3) * 32 + o) * CIN;
+#pragma unroll
+                for (int c = 0; c < CIN; ++c) atomicAdd(d + c, v[c]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)S::TCOLS)
+                     : "memory");
+    }
+    if (tid == 0 && s_err) atomicExch(&g_tc_error, 1);
+}
+
 // ---- host side ---------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -490,15 +690,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// [N][Z][Y][X][C] BF16 activations as a 5-D tensor map, box C channels x 32
-// voxels, 64-byte (C = 32) or 32-byte (C = 16) swizzle.
-bool make_map(CUtensorMap *m, const void *base, int C, int X, int Y, int Z, int N) {
+// [N][Z][Y][X][C] BF16 activations as a 5-D tensor map, box C channels x
+// box_x voxels, 64-byte (C = 32) or 32-byte (C = 16) swizzle.
+bool make_map(CUtensorMap *m, const void *base, int C, int X, int Y, int Z, int N, int box_x = 32) {
     auto fn = encode_fn();
     if (!fn || ((uintptr_t)base & 15u)) return false;
     const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)Z, (cuuint64_t)N};
     const cuuint64_t row = (cuuint64_t)C * 2;
     const cuuint64_t strides[4] = {row, row * X, row * X * Y, row * X * Y * Z};
-    const cuuint32_t box[5] = {(cuuint32_t)C, 32, 1, 1, 1};
+    const cuuint32_t box[5] = {(cuuint32_t)C, (cuuint32_t)box_x, 1, 1, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
@@ -558,7 +758,43 @@ cudaError_t dispatch_tc(const float *w, const float *bias, void *y, const TcPara
     return cudaErrorInvalidValue;
 }
 
+template <int CIN>
+cudaError_t run_wgrad_tc(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, cudaStream_t s) {
+    using S = WgShape<CIN>;
+    WgParams p;
+    memset(&p, 0, sizeof(p));
+    if (!make_map(&p.mx, x, CIN, X, Y, Z, N, WG_K) || !make_map(&p.mg, gy, 32, X, Y, Z, N, WG_K))
+        return cudaErrorInvalidValue;
+    p.Z = Z;
+    p.Y = Y;
+    p.nxc = (X + WG_K - 1) / WG_K;
+    const long long items = (long long)N * Z * Y * p.nxc;
+    if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (items == 0) return cudaSuccess;
+    p.items = (int)items;
+    auto kern = k_conv3d_wgrad_tc<CIN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
+    long long grid = sm_count_tc();
+    if (grid > items) grid = items;
+    kern<<<(unsigned)grid, WG_THREADS, S::SMEM, s>>>(dw, p);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool wgrad_tc_supported(int cin, int cout, int X) {
+    return (cin == 16 || cin == 32) && cout == 32 && X >= WG_K && encode_fn() != nullptr;
+}
+
+// dw += the weight gradient (zeroed by the caller when it starts afresh);
+// x and gy 16-byte aligned, wgrad_tc_supported(cin, cout, X).
+cudaError_t launch_conv3d_wgrad_tc(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, int cin,
+                                   int cout, cudaStream_t s) {
+    if (!wgrad_tc_supported(cin, cout, X) || (((uintptr_t)x | (uintptr_t)gy) & 15u)) return cudaErrorInvalidValue;
+    return cin == 32 ? run_wgrad_tc<32>(x, gy, dw, N, Z, Y, X, s) : run_wgrad_tc<16>(x, gy, dw, N, Z, Y, X, s);
+}
 
 bool conv_tc_supported(int cin, int cout) {
     return (cin == 16 || cin == 32) && (cout == 8 || cout == 16 || cout == 32) && !(cin == 16 && cout == 8) &&

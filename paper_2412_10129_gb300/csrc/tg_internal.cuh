@@ -200,6 +200,9 @@ cudaError_t launch_conv3d_ragged(const void *x, const float *w, const float *bia
                                  int nvol, int cin, int cout, int relu, int out_f32, cudaStream_t s);
 // Tensor-core (tcgen05 + TMA) convolutions, tg_conv_tc.cu.
 bool conv_tc_supported(int cin, int cout);
+bool wgrad_tc_supported(int cin, int cout, int X);
+cudaError_t launch_conv3d_wgrad_tc(const void *x, const void *gy, float *dw, int N, int Z, int Y, int X, int cin,
+                                   int cout, cudaStream_t s);
 cudaError_t launch_conv3d_tc(const void *x, const float *w, const float *bias, void *y, int N, int Z, int Y, int X,
                              int cin, int cout, int relu, int out_f32, cudaStream_t s);
 cudaError_t launch_conv3d_tc_ragged(const void *x, const float *w, const float *bias, void *y, const int *dims,

@@ -236,6 +236,29 @@ def test_conv_backward_weight_and_bias_match_oracle(cin, cout):
     assert rel_l2(db, gyo.sum(axis=(0, 1, 2, 3))) <= 1e-5
 
 
+@pytest.mark.parametrize("cin", [16, 32])
+def test_conv_backward_weight_many_items_per_cta(cin):
+    """The tensor-core weight gradient keeps its sums in tensor memory over
+    all of a CTA's items: a volume with several items per CTA (12 x 14 rows
+    of 200 voxels = 3 full 64-voxel chunks and a ragged one per row), two
+    volumes, against the FP64 oracle; and the same gradient through the
+    mma.sync kernel."""
+    import os
+    rng = np.random.default_rng(41 + cin)
+    x, xo = bf16_input(rng, (2, 12, 14, 200, cin))
+    gy, gyo = bf16_input(rng, (2, 12, 14, 200, 32))
+    ref = oconv.conv3d_backward_weight(xo, gyo)
+    dw = tg.conv3d_backward_weight(x, gy).cpu().numpy()
+    assert rel_l2(to_oracle_w(dw), ref) <= 1e-5, rel_l2(to_oracle_w(dw), ref)
+    os.environ["TG_CONV_IMPL"] = "mma"
+    try:
+        dm = tg.conv3d_backward_weight(x, gy).cpu().numpy()
+    finally:
+        del os.environ["TG_CONV_IMPL"]
+    assert rel_l2(to_oracle_w(dm), ref) <= 1e-5
+    assert rel_l2(dw, dm) <= 1e-5
+
+
 def test_elementwise_kernels():
     rng = np.random.default_rng(17)
     g, go = bf16_input(rng, (3, 4, 5, 32))
