@@ -452,12 +452,17 @@ __global__ void __launch_bounds__(MT, 1)
                                      __uint_as_float(ep.absmax[b]), bl % nbx, (bl / nbx) % nby, bl / (nbx * nby));
 }
 
-// A ray of the current angle with samples in a brick, in 8 bytes: y is read
-// again when a lane takes the ray.  iuv = iu | iv << 16; kk = ka | (kc - ka)
-// << 20 | class << 31 (ka < 2^20, kc - ka < 2^11: checked on the host).
-struct RayRec8 {
-    unsigned int iuv;
-    unsigned int kk;
+// A ray of the current angle with samples in a brick, in 32 bytes: its
+// frame (the forward projector's FP32 reference point and step, index
+// space), its y (times its accumulator class's scale) and kk = (ka - kr) &
+// 0xfffff | (kc - ka) << 20 | class << 31, with ka - kr in 20 bits signed
+// and kc - ka < 2^11 (both checked on the host).  The frame is the one the
+// list builder computed to find the ray's samples; keeping it spares the
+// lane that later takes the ray a second double-float set-up, which ran
+// divergently (one or two lanes of a warp at a time).
+struct __align__(16) RayRecF {
+    float4 s;  // sx, sy, sz, gx
+    float4 t;  // gy, gz, y, kk (bits)
 };
 constexpr int LONG_RAY = 32;  // list order: rays of at least this many samples first
 
@@ -503,10 +508,12 @@ struct Mx {
     static constexpr int NRIM = F1 + F2 + F3;
     static constexpr int RIM_PER_THREAD = (NRIM + XT - 1) / XT;
     static constexpr int OWN = XB * YB * ZB / XT;                // owned voxels per thread
-    static constexpr int SMEM = 2 * WORDS * 4 + RAYCAP * (int)sizeof(RayRec8);
+    static constexpr int SMEM = 2 * WORDS * 4 + RAYCAP * (int)sizeof(RayRecF);
+    // largest local index of a cell's first corner (lx <= XB, ly <= YB, lz <= ZB)
+    static constexpr unsigned LINMAX = ZB * PP + YB * PX + XB;
     static constexpr int MINB = 1024 / XT;                       // CTAs per SM: 1024 threads at 64 registers
     static_assert(XB == 32 && NW * YR == YB && OWN == YR * ZB, "owned map: lane = x, warp + NW j = y");
-    static_assert(RAYCAP >= 2 * XT, "a chunk takes at least one full step of candidates");
+    static_assert(RAYCAP > XT && (2 * WORDS * 4) % 16 == 0, "a chunk takes at least one full step of candidates");
     // rim index of accumulator voxel (lx, ly, lz) (local = voxel - o + 1; at
     // least one coordinate B + 1, the others in 1 .. B + 1) and its inverse
     __host__ __device__ static int rim_index(int lx, int ly, int lz) {
@@ -543,11 +550,13 @@ __device__ __forceinline__ bool cell_in(const Ray &r, int k, float lox, float lo
 }
 
 // The samples of ray (iu, iv) whose cells lie in [lo, hi) (cell units,
-// exact), as a compact record; false when there are none or y = 0.
+// exact), as a list record; false when there are none or y = 0.  y goes
+// to the first class (scaled by sc_big) when |y| > ybig, else to the second
+// (sc_fine).
 template <bool PAR>
 __device__ __forceinline__ bool region_ray_x(const Angle &A, const Grid &g, float yraw, int iu, int iv, bool edge,
                                              float lox, float loy, float loz, float hix, float hiy, float hiz,
-                                             float ybig, RayRec8 &rec, int &len) {
+                                             float ybig, float sc_big, float sc_fine, RayRecF &rec, int &len) {
     if (yraw == 0.f) return false;
     Ray r;
     int kb0 = 0, kb1 = 0x7fffffff;
@@ -586,8 +595,10 @@ __device__ __forceinline__ bool region_ray_x(const Angle &A, const Grid &g, floa
     for (int t = 0; t < 4 && kc >= ka && !cell_in(r, kc, lox, loy, loz, hix, hiy, hiz); ++t) --kc;
     if (ka > kc) return false;
     const bool big = fabsf(yraw) > ybig;
-    rec.iuv = (unsigned int)iu | ((unsigned int)iv << 16);
-    rec.kk = (unsigned int)ka | ((unsigned int)(kc - ka) << 20) | (big ? 0x80000000u : 0u);
+    const unsigned int kk =
+        ((unsigned int)(ka - r.kr) & 0xfffffu) | ((unsigned int)(kc - ka) << 20) | (big ? 0x80000000u : 0u);
+    rec.s = make_float4(r.sx, r.sy, r.sz, r.gx);
+    rec.t = make_float4(r.gy, r.gz, yraw * (big ? sc_big : sc_fine), __uint_as_float(kk));
     len = kc - ka + 1;
     return true;
 }
@@ -602,22 +613,28 @@ __device__ __forceinline__ void split_add(unsigned int *c, int lo_off, float p, 
     atomicAdd(c + lo_off, (unsigned int)(__float_as_int(fmaf(t - hi, two_m, MAGIC)) - MAGIC_BITS));
 }
 
-// One sample's eight contributions into the exclusive-cell accumulator;
-// mo* = MAGIC_BITS + o* - 1 (local index = voxel - o + 1).
+// One sample's eight contributions into the exclusive-cell accumulator.
+// The local index of the cell's first corner, (cz - oz + 1) PP + (cy - oy +
+// 1) PX + (cx - ox + 1), comes from the integer bits of c + MAGIC in
+// wrapping unsigned arithmetic (kbase holds the origin's part).  Every
+// listed sample's cell lies in the brick; the clamp only keeps the padding
+// sample of an odd-length run (weight 0, possibly past the brick) inside
+// the accumulator.
 template <class C, int ACC>
 __device__ __forceinline__ void scatter_x(unsigned int *accc, float kf, float gx, float gy, float gz, float sx,
-                                          float sy, float sz, float ys, int mox, int moy, int moz, float scale,
+                                          float sy, float sz, float ys, unsigned int kbase, float scale,
                                           float two_m) {
     const float x = fmaf(kf, gx, sx), yy = fmaf(kf, gy, sy), z = fmaf(kf, gz, sz);
     const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
-    const int lx = min(max(__float_as_int(fx + MAGIC) - mox, 0), C::XB);
-    const int ly = min(max(__float_as_int(fy + MAGIC) - moy, 0), C::YB);
-    const int lz = min(max(__float_as_int(fz + MAGIC) - moz, 0), C::ZB);
+    const unsigned int lin = min(__float_as_uint(fz + MAGIC) * (unsigned int)C::PP +
+                                     __float_as_uint(fy + MAGIC) * (unsigned int)C::PX + __float_as_uint(fx + MAGIC) -
+                                     kbase,
+                                 C::LINMAX);
     const float wx = x - fx, wy = yy - fy, wz = z - fz;
     const float c0 = ys * (1.f - wz), c1 = ys * wz;
     const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
     const float ux = 1.f - wx;
-    unsigned int *c = accc + lz * C::PP + ly * C::PX + lx;
+    unsigned int *c = accc + lin;
     if (ACC == ACC_SPLIT) {  // ys is the raw y here; each product is split
         split_add(c, C::WORDS, b00 * ux, scale, two_m);
         split_add(c + 1, C::WORDS, b00 * wx, scale, two_m);
@@ -665,7 +682,7 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
     const float hix = (float)(x0 + C::XB), hiy = (float)(y0 + C::YB), hiz = (float)(z0 + C::ZB);
     const bool edge =
         x0 == 0 || y0 == 0 || z0 == 0 || x0 + C::XB >= g.nx || y0 + C::YB >= g.ny || z0 + C::ZB >= g.nz;
-    RayRec8 *rays = reinterpret_cast<RayRec8 *>(acc + 2 * C::WORDS);
+    RayRecF *rays = reinterpret_cast<RayRecF *>(acc + 2 * C::WORDS);
     __shared__ int s_cnt[3];
     __shared__ Angle sA;
     const bool nonfinite = !(gmax <= 3.4028235e38f);
@@ -676,9 +693,14 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
     // word holds fractions of the first's unit at 2^m with 2^(m-1) wbound <= 2^30
     const float two_m = exp2f(fminf(floorf(31.f - log2f(g.wbound)), 22.f));
     const float scale_f = ACC == ACC_SPLIT ? 1.f : FINE * scale;
+    const float sc_big = ACC == ACC_SPLIT ? 1.f : scale;
     const float k1 = inv_scale, k2 = ACC == ACC_SPLIT ? inv_scale / two_m : inv_scale * (1.f / FINE);
     const float ybig = ACC == ACC_SPLIT ? -1.f : gmax * (1.f / FINE);
-    const int mox = MAGIC_BITS + x0 - 1, moy = MAGIC_BITS + y0 - 1, moz = MAGIC_BITS + z0 - 1;
+    // the integer bits of c + MAGIC for cell c, minus those of the accumulator
+    // origin (o - 1), combined with the pitches (wrapping unsigned arithmetic)
+    const unsigned int kbase = (unsigned int)(MAGIC_BITS + z0 - 1) * (unsigned int)C::PP +
+                               (unsigned int)(MAGIC_BITS + y0 - 1) * (unsigned int)C::PX +
+                               (unsigned int)(MAGIC_BITS + x0 - 1);
     float own[C::OWN], rimv[C::RIM_PER_THREAD];
 #pragma unroll
     for (int j = 0; j < C::OWN; ++j) own[j] = 0.f;
@@ -712,8 +734,15 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
         const int v0 = max((int)ceilf(vmin - 1e-3f), 0), v1 = min((int)floorf(vmax + 1e-3f), g.nv - 1);
         if (u1 >= u0 && v1 >= v0) {
             const float *pa = pb + (size_t)a * g.nv * g.nu;
-            const int ntu = (u1 - u0 + 32) >> 5, ntv = (v1 - v0 + 16) >> 4;
-            const int ncand = ntu * ntv * 16 * 32;
+            // candidates: the bounding box in tiles of 16 x 8 pixels; a warp's 32
+            // candidates are an 8 x 4 lattice of stride 2 (four phases per tile),
+            // so lanes that take consecutive list entries get rays two pixels
+            // apart (measured on the 512^3 scan: 5 % faster than 32 x 16 tiles of
+            // stride 4, whose rounding adds more empty candidates; a row-major
+            // order of the exact box, with neighbouring rays side by side, 2 %
+            // slower than those)
+            const int ntu = (u1 - u0 + 16) >> 4, ntv = (v1 - v0 + 8) >> 3;
+            const int ncand = ntu * ntv * 4 * 32;
             for (int c0 = 0; c0 < ncand;) {
                 if (tid == 0) {
                     s_cnt[0] = 0;
@@ -725,15 +754,15 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
                     const int cand = c0 + tid;
                     bool keep = false;
                     int len = 0;
-                    RayRec8 rec;
+                    RayRecF rec;
                     if (cand < ncand) {
                         const int task = cand >> 5, slot = cand & 31;
-                        const int ph = task & 15, tile = task >> 4;
-                        const int iu = u0 + (tile % ntu) * 32 + (slot & 7) * 4 + (ph & 3);
-                        const int iv = v0 + (tile / ntu) * 16 + (slot >> 3) * 4 + (ph >> 2);
+                        const int ph = task & 3, tile = task >> 2;
+                        const int iu = u0 + (tile % ntu) * 16 + (slot & 7) * 2 + (ph & 1);
+                        const int iv = v0 + (tile / ntu) * 8 + (slot >> 3) * 2 + (ph >> 1);
                         if (iu <= u1 && iv <= v1)
                             keep = region_ray_x<PAR>(A, g, __ldg(pa + (size_t)iv * g.nu + iu), iu, iv, edge, lox,
-                                                     loy, loz, hix, hiy, hiz, ybig, rec, len);
+                                                     loy, loz, hix, hiy, hiz, ybig, sc_big, scale_f, rec, len);
                     }
                     // long rays from the front of the list, short ones from the back
                     const bool lg = keep && len >= LONG_RAY;
@@ -769,24 +798,18 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
                         if (need) {
                             const int idx = base + __popc(m & ((1u << lane) - 1u));
                             if (idx < nr) {
-                                const RayRec8 rr = rays[idx < nl ? idx : C::RAYCAP - 1 - (idx - nl)];
-                                const int iu = (int)(rr.iuv & 0xffffu), iv = (int)(rr.iuv >> 16);
-                                Ray q;
-                                float Ld;
-                                ray_frame<PAR>(A, g, iu, iv, q, Ld);
-                                gx = q.gx;
-                                gy = q.gy;
-                                gz = q.gz;
-                                sx = q.sx;
-                                sy = q.sy;
-                                sz = q.sz;
-                                const bool bigr = (rr.kk >> 31) != 0;
-                                const float yv = __ldg(pa + (size_t)iv * g.nu + iu);
-                                ys = ACC == ACC_SPLIT ? yv : yv * (bigr ? scale : scale_f);
-                                const int ka = (int)(rr.kk & 0xfffffu);
-                                k = ka - q.kr;
-                                kc = ka + (int)((rr.kk >> 20) & 0x7ffu) - q.kr;
-                                accc = (ACC == ACC_SPLIT || bigr) ? acc : acc + C::WORDS;
+                                const RayRecF rr = rays[idx < nl ? idx : C::RAYCAP - 1 - (idx - nl)];
+                                sx = rr.s.x;
+                                sy = rr.s.y;
+                                sz = rr.s.z;
+                                gx = rr.s.w;
+                                gy = rr.t.x;
+                                gz = rr.t.y;
+                                ys = rr.t.z;
+                                const unsigned int kk = __float_as_uint(rr.t.w);
+                                k = ((int)(kk << 12)) >> 12;  // ka - kr
+                                kc = k + (int)((kk >> 20) & 0x7ffu);
+                                accc = (ACC == ACC_SPLIT || (kk >> 31) != 0) ? acc : acc + C::WORDS;
                             } else {
                                 live = false;
                             }
@@ -795,9 +818,9 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
                     const float kf = (float)k;
-                    scatter_x<C, ACC>(accc, kf, gx, gy, gz, sx, sy, sz, ys, mox, moy, moz, scale, two_m);
-                    scatter_x<C, ACC>(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, mox, moy, moz,
-                                      scale, two_m);
+                    scatter_x<C, ACC>(accc, kf, gx, gy, gz, sx, sy, sz, ys, kbase, scale, two_m);
+                    scatter_x<C, ACC>(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, kbase, scale,
+                                      two_m);
                     k += 2;
                 }
                 __syncthreads();
@@ -1004,7 +1027,7 @@ cudaError_t launch_mx(const Grid &g, const Angle *d_angles, const float *proj, f
 
 // One 1024-thread CTA per SM (measured faster than two 512-thread CTAs on
 // 32x16x16 bricks: 3.09 s against 3.28 s for the 512^3 / 720-view scan).
-using MxA = Mx<32, 32, 16, 1024, 2048>;
+using MxA = Mx<32, 32, 16, 1024, 1792>;
 
 // Volumes of different sizes and geometries in one launch (packed back to
 // back): blocks blk0[v] .. blk0[v + 1] - 1 are volume v's bricks.
@@ -1138,7 +1161,7 @@ cudaError_t launch_matched(dim3 grid, const float *proj, float *vol, const Angle
 bool mx_fits(const Grid &g) {
     const double chord = sqrt((double)(MxA::XA * MxA::XA) * g.dx * g.dx + (double)(MxA::YA * MxA::YA) * g.dy * g.dy +
                               (double)(MxA::ZA * MxA::ZA) * g.dz * g.dz) / (double)g.delta + 2.0;
-    return g.kmax < 1048000.f && chord < 2000.0 && g.nu <= 65535 && g.nv <= 65535;
+    return g.kmax < 524000.f && chord < 2000.0 && g.nu <= 65535 && g.nv <= 65535;
 }
 
 // Ragged exclusive-cell backprojection of n <= MXR_MAXV volumes (32-bit
