@@ -126,6 +126,31 @@ __device__ __noinline__ bool ray_setup_outlined(const Angle &A, const Grid &g, i
     return ray_setup<PAR>(A, g, iu, iv, r);
 }
 
+// Every ray's set-up (the forward projector's frame and its first and last
+// kept sample), computed once per ray for the exclusive-cell bricks' list
+// builders, which would otherwise rebuild it in every brick the ray passes
+// near.  Entry ((a nv + iv) nu + iu): fa = (sx, sy, sz, gx), fb = (gy, gz,
+// kr, k0) (ints as bits), fc = k1; k0 > k1 when no sample is kept.
+struct RayTable {
+    const float4 *fa;
+    const float4 *fb;
+    const int *fc;
+};
+
+template <bool PAR>
+__global__ void __launch_bounds__(256) k_ray_table(const Angle *__restrict__ angles, Grid g, float4 *fa, float4 *fb,
+                                                   int *fc) {
+    const size_t per = (size_t)g.nv * g.nu, n = per * g.nA;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(i / per), iv = (int)((i % per) / g.nu), iu = (int)(i % g.nu);
+        Ray r;
+        ray_setup<PAR>(angles[a], g, iu, iv, r);
+        fa[i] = make_float4(r.sx, r.sy, r.sz, r.gx);
+        fb[i] = make_float4(r.gy, r.gz, __int_as_float(r.kr), __int_as_float(r.k0));
+        fc[i] = r.k1;
+    }
+}
+
 constexpr int BX = 32, BY = 32, BZ = 16;              // owned voxels per brick
 constexpr int RIM = 2;                                // allocated rim per side (voxels)
 constexpr int RX = BX + 2 * RIM, RY = BY + 2 * RIM, RZ = BZ + 2 * RIM;
@@ -556,11 +581,24 @@ __device__ __forceinline__ bool cell_in(const Ray &r, int k, float lox, float lo
 template <bool PAR>
 __device__ __forceinline__ bool region_ray_x(const Angle &A, const Grid &g, float yraw, int iu, int iv, bool edge,
                                              float lox, float loy, float loz, float hix, float hiy, float hiz,
-                                             float ybig, float sc_big, float sc_fine, RayRecF &rec, int &len) {
+                                             float ybig, float sc_big, float sc_fine, const RayTable &tb, size_t ti,
+                                             RayRecF &rec, int &len) {
     if (yraw == 0.f) return false;
     Ray r;
     int kb0 = 0, kb1 = 0x7fffffff;
-    if (edge) {
+    if (tb.fa) {  // the same set-up, from the table (interior bricks' samples are all kept)
+        const float4 p = __ldg(tb.fa + ti), q = __ldg(tb.fb + ti);
+        kb0 = __float_as_int(q.w);
+        kb1 = __ldg(tb.fc + ti);
+        if (kb0 > kb1) return false;
+        r.sx = p.x;
+        r.sy = p.y;
+        r.sz = p.z;
+        r.gx = p.w;
+        r.gy = q.x;
+        r.gz = q.y;
+        r.kr = __float_as_int(q.z);
+    } else if (edge) {
         if (!ray_setup_outlined<PAR>(A, g, iu, iv, r)) return false;
         kb0 = r.k0;
         kb1 = r.k1;
@@ -668,11 +706,12 @@ __device__ __forceinline__ float take_x(unsigned int *acc, int o, float k1, floa
 
 // Brick (bx, by, bz) of one volume: pb its projections, sv its owned sums
 // (unscaled, one FP32 per voxel of the volume), rb the brick's NRIM rim
-// sums, gmax the max |y| of its projections.
+// sums, gmax the max |y| of its projections, tb its rays' set-ups (or
+// none: each brick then builds them itself).
 template <class C, int ACC, bool PAR>
 __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__restrict__ sv, float *__restrict__ rb,
                                          const Angle *__restrict__ angles, const Grid &g, float gmax, int bx, int by,
-                                         int bz) {
+                                         int bz, const RayTable &tb) {
     extern __shared__ unsigned int acc[];
     constexpr int XT = C::XT, NW = C::NW, YR = C::YR;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -762,7 +801,8 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
                         const int iv = v0 + (tile / ntu) * 8 + (slot >> 3) * 2 + (ph >> 1);
                         if (iu <= u1 && iv <= v1)
                             keep = region_ray_x<PAR>(A, g, __ldg(pa + (size_t)iv * g.nu + iu), iu, iv, edge, lox,
-                                                     loy, loz, hix, hiy, hiz, ybig, sc_big, scale_f, rec, len);
+                                                     loy, loz, hix, hiy, hiz, ybig, sc_big, scale_f, tb,
+                                                     ((size_t)a * g.nv + iv) * g.nu + iu, rec, len);
                     }
                     // long rays from the front of the list, short ones from the back
                     const bool lg = keep && len >= LONG_RAY;
@@ -863,11 +903,11 @@ template <class C, int ACC, bool PAR>
 __global__ void __launch_bounds__(C::XT, C::MINB)
     k_bp_mx(const float *__restrict__ proj, float *__restrict__ sumv, float *__restrict__ rim,
             const Angle *__restrict__ angles, Grid g, const unsigned int *__restrict__ absmax, int nbx, int nby,
-            int nbricks) {
+            int nbricks, RayTable tb) {
     const int b = blockIdx.y, bl = blockIdx.x;
     mx_brick<C, ACC, PAR>(proj + (size_t)b * g.nA * g.nv * g.nu, sumv + (size_t)b * g.nx * g.ny * g.nz,
                           rim + ((size_t)b * nbricks + bl) * C::NRIM, angles, g, __uint_as_float(absmax[b]), bl % nbx,
-                          (bl / nbx) % nby, bl / (nbx * nby));
+                          (bl / nbx) % nby, bl / (nbx * nby), tb);
 }
 
 // Volumes of different sizes and geometries in one launch (packed back to
@@ -904,7 +944,7 @@ __global__ void __launch_bounds__(C::XT, C::MINB)
     const int bl = blockIdx.x - tab.blk0[v], nbx = tab.nbx[v], nby = tab.nby[v];
     mx_brick<C, ACC, PAR>(proj + tab.p0[v], sumv + tab.v0[v], rim + tab.r0[v] + (size_t)bl * C::NRIM,
                           angles + tab.a0[v], tab.g[v], __uint_as_float(absmax[v]), bl % nbx, (bl / nbx) % nby,
-                          bl / (nbx * nby));
+                          bl / (nbx * nby), RayTable{nullptr, nullptr, nullptr});
 }
 
 // Owner sum of voxel i of a volume plus the rims of its up to seven lower
@@ -985,17 +1025,42 @@ cudaError_t launch_mx(const Grid &g, const Angle *d_angles, const float *proj, f
         return cudaErrorMemoryAllocation;
     }
     if (in_place) sumv = vol;
-    KernelTimer kt(ACC == ACC_SPLIT ? TG_KT_BP_MATCHED_SPLIT : TG_KT_BP_MATCHED, s);  // bricks and merge
+    KernelTimer kt(ACC == ACC_SPLIT ? TG_KT_BP_MATCHED_SPLIT : TG_KT_BP_MATCHED, s);  // table, bricks and merge
+    // the rays' set-ups, 36 bytes per ray and angle, when they fit in half
+    // of the free device memory (otherwise every brick builds its own)
+    RayTable tb{nullptr, nullptr, nullptr};
+    void *tbuf = nullptr;
     {
+        const size_t nray = (size_t)g.nA * g.nv * g.nu;
+        const size_t bytes = nray * 36 + 64;
+        size_t fr = 0, tot = 0;
+        if (nray > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes <= fr / 2 &&
+            cudaMallocAsync(&tbuf, bytes, s) == cudaSuccess) {
+            float4 *fa = reinterpret_cast<float4 *>(tbuf), *fb = fa + nray;
+            int *fc = reinterpret_cast<int *>(fb + nray);
+            const size_t nb = (nray + 255) / 256;
+            const unsigned grid = (unsigned)(nb < 152 * 64 ? nb : 152 * 64);
+            if (g.parallel) k_ray_table<true><<<grid, 256, 0, s>>>(d_angles, g, fa, fb, fc);
+            else k_ray_table<false><<<grid, 256, 0, s>>>(d_angles, g, fa, fb, fc);
+            count_launch();
+            e = cudaGetLastError();
+            tb = RayTable{fa, fb, fc};
+        } else {
+            cudaGetLastError();
+            tbuf = nullptr;
+        }
+    }
+    if (e == cudaSuccess) {
         auto kern = g.parallel ? k_bp_mx<C, ACC, true> : k_bp_mx<C, ACC, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e == cudaSuccess) {
             kern<<<dim3((unsigned)nbricks, batch), C::XT, C::SMEM, s>>>(proj, sumv, rim, d_angles, g, ep.absmax, nbx,
-                                                                        nby, nbricks);
+                                                                        nby, nbricks, tb);
             count_launch();
             e = cudaGetLastError();
         }
     }
+    if (tbuf) cudaFreeAsync(tbuf, s);
     if (e == cudaSuccess) {
         size_t nb = (nvox + 255) / 256;
         if (nb > 152 * 16) nb = 152 * 16;

@@ -90,8 +90,9 @@ def test_batch_of_16_in_one_launch():
     n0 = tg.launch_count()
     vb = ag().backproject(pb, g)
     torch.cuda.synchronize()
-    # max-|y| pre-pass, one brick launch for the batch, the merge of the bricks' rims
-    assert tg.launch_count() - n0 == 3
+    # max-|y| pre-pass, the rays' set-up table (shared by the batch), one brick
+    # launch for the batch, the merge of the bricks' rims
+    assert tg.launch_count() - n0 == 4
     for i in (0, 15):
         torch.testing.assert_close(vb[i], tg.backproject(g, pb[i].contiguous(), "matched"), rtol=0, atol=0)
 
