@@ -694,6 +694,59 @@ __device__ __forceinline__ void scatter_x(unsigned int *accc, float kf, float gx
     }
 }
 
+// Two consecutive samples of one ray for the split-word accumulation (16
+// atomics per sample): when both fall in the same cell (about 43 % of
+// consecutive pairs) their eight products are summed first and half of
+// the atomics fall away.  Measured on the 512^3 scan: 3 % faster for the
+// split words, 3.5 % slower for the 8-atomic fixed point, where the extra
+// compare and selects cost more issue slots than the atomics saved.
+template <class C, int ACC>
+__device__ __forceinline__ void scatter_pair(unsigned int *accc, float kf, float gx, float gy, float gz, float sx,
+                                             float sy, float sz, float ya, float yb, unsigned int kbase, float scale,
+                                             float two_m) {
+    float w[2][8];
+    unsigned int ci[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float kk = kf + (float)h;
+        const float x = fmaf(kk, gx, sx), yy = fmaf(kk, gy, sy), z = fmaf(kk, gz, sz);
+        const float fx = floorf(x), fy = floorf(yy), fz = floorf(z);
+        ci[h] = min(__float_as_uint(fz + MAGIC) * (unsigned int)C::PP + __float_as_uint(fy + MAGIC) * (unsigned int)C::PX +
+                        __float_as_uint(fx + MAGIC) - kbase,
+                    C::LINMAX);
+        const float wx = x - fx, wy = yy - fy, wz = z - fz;
+        const float ys = h ? yb : ya;
+        const float c0 = ys * (1.f - wz), c1 = ys * wz;
+        const float b00 = c0 * (1.f - wy), b01 = c0 * wy, b10 = c1 * (1.f - wy), b11 = c1 * wy;
+        const float ux = 1.f - wx;
+        w[h][0] = b00 * ux;
+        w[h][1] = b00 * wx;
+        w[h][2] = b01 * ux;
+        w[h][3] = b01 * wx;
+        w[h][4] = b10 * ux;
+        w[h][5] = b10 * wx;
+        w[h][6] = b11 * ux;
+        w[h][7] = b11 * wx;
+    }
+    const bool same = ci[0] == ci[1];
+    const int off[8] = {0, 1, C::PX, C::PX + 1, C::PP, C::PP + 1, C::PP + C::PX, C::PP + C::PX + 1};
+    unsigned int *c = accc + ci[0];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float p = same ? w[0][q] + w[1][q] : w[0][q];
+        if (ACC == ACC_SPLIT) split_add(c + off[q], C::WORDS, p, scale, two_m);
+        else atomicAdd(c + off[q], (unsigned int)(__float_as_int(p + MAGIC) - MAGIC_BITS));
+    }
+    if (!same) {
+        c = accc + ci[1];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (ACC == ACC_SPLIT) split_add(c + off[q], C::WORDS, w[1][q], scale, two_m);
+            else atomicAdd(c + off[q], (unsigned int)(__float_as_int(w[1][q] + MAGIC) - MAGIC_BITS));
+        }
+    }
+}
+
 // Reads (and clears) one accumulator voxel as FP32 in units of y; k1, k2 the
 // factors of the first and the second word.
 template <class C>
@@ -858,9 +911,14 @@ __device__ __forceinline__ void mx_brick(const float *__restrict__ pb, float *__
                     if (!__any_sync(0xffffffffu, live)) break;
                     if (!live) continue;
                     const float kf = (float)k;
-                    scatter_x<C, ACC>(accc, kf, gx, gy, gz, sx, sy, sz, ys, kbase, scale, two_m);
-                    scatter_x<C, ACC>(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, kbase, scale,
-                                      two_m);
+                    if (ACC == ACC_SPLIT) {
+                        scatter_pair<C, ACC>(accc, kf, gx, gy, gz, sx, sy, sz, ys, k + 1 <= kc ? ys : 0.f, kbase, scale,
+                                             two_m);
+                    } else {
+                        scatter_x<C, ACC>(accc, kf, gx, gy, gz, sx, sy, sz, ys, kbase, scale, two_m);
+                        scatter_x<C, ACC>(accc, kf + 1.f, gx, gy, gz, sx, sy, sz, k + 1 <= kc ? ys : 0.f, kbase, scale,
+                                          two_m);
+                    }
                     k += 2;
                 }
                 __syncthreads();
