@@ -34,7 +34,12 @@
  * stream has finished); the batched, TV and network calls take device
  * memory only.  The caller owns every buffer; the library never frees
  * them.  Scratch memory is taken with cudaMallocAsync on `stream` and
- * released before return (tg_workspace_size reports how much).
+ * released before return (tg_workspace_size reports how much).  The
+ * matched backprojection (TG_MATCHED, also inside the solvers) may take,
+ * in addition, a table of its rays' set-ups, 36 bytes per ray and angle
+ * of the call (20 GB for 720 views of 768 x 1024 pixels), but only when
+ * that fits in half of the device memory free at the call; otherwise it
+ * works without it, at the same results.
  *
  * Errors: argument and geometry checks run on the host before any launch
  * and return synchronously; kernel launch errors are read with

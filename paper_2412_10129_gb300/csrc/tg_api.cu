@@ -1055,6 +1055,11 @@ tg_status tg_workspace_size(const tg_geometry *geo, int nAngles, int op, int bat
         case 10: f = ang + 4 * (2 * nray + 4 * nvox) + 192; break;  // lsmr
         default: return TG_ERR_ARG;
     }
+    // the matched backprojection's brick sums (in place for A^T y and CGLS-type
+    // updates, a separate volume for the SIRT / EM epilogues)
+    const int nx = geo->nVoxel[0], ny = geo->nVoxel[1], nz = geo->nVoxel[2];
+    const bool in_place = op == 1 || op == 5 || op == 9 || op == 10;
+    if (op != 0 && op != 2) f += matched_scratch_bytes(nx, ny, nz, batch, in_place);
     *bytes = f;
     return TG_OK;
 }

@@ -1354,6 +1354,16 @@ cudaError_t launch_mx_ragged(const Grid *gs, const float *scales, int n, const i
 
 }  // namespace
 
+// Scratch of one exclusive-cell backprojection beyond the angle constants:
+// the rim sums of every brick, plus the owned sums when the epilogue does
+// not store in place (the optional ray table is not counted).
+size_t matched_scratch_bytes(int nx, int ny, int nz, int batch, bool in_place) {
+    const size_t nb = (size_t)((nx + MxA::XB - 1) / MxA::XB) * (size_t)((ny + MxA::YB - 1) / MxA::YB) *
+                      (size_t)((nz + MxA::ZB - 1) / MxA::ZB);
+    const size_t b = (size_t)(batch > 0 ? batch : 1);
+    return 4 * (size_t)MxA::NRIM * nb * b + (in_place ? 0 : 4 * (size_t)nx * ny * nz * b) + 512;
+}
+
 cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles, const float *proj, float *vol,
                                int batch, int mode, const BpEpilogue &ep, cudaStream_t s) {
     if (batch == 0) return cudaSuccess;

@@ -167,6 +167,7 @@ cudaError_t launch_forward(int method, const Grid &g, const Angle *d_angles, con
 // volume v in d_angles.  Modes FP_STORE and FP_RESID_W (W null).
 cudaError_t launch_forward_ragged(const Grid *gs, int nvol, const int *angle0, const Angle *d_angles, const float *vol,
                                   float *proj, int mode, const FpEpilogue &ep, cudaStream_t s);
+size_t matched_scratch_bytes(int nx, int ny, int nz, int batch, bool in_place);
 cudaError_t launch_backproject(int method, const Grid &g, const Angle *d_angles, const float *proj,
                                float *vol, int batch, int mode, const BpEpilogue &ep,
                                cudaStream_t s);

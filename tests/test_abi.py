@@ -125,6 +125,12 @@ def test_workspace_size(lib):
     assert tg.workspace_size(g, "cgls") >= 4 * (2 * nray + 2 * nvox)
     assert tg.workspace_size(g, "ossart", blocksize=20) >= 4 * nvox * 36
     assert tg.workspace_size(g, "forward") < 1 << 20
+    # the matched backprojection's brick rims: 2129 upper-face voxels per
+    # 32 x 32 x 16 brick (16 x 16 x 32 bricks), owned sums in place
+    rims = 4 * 2129 * 16 * 16 * 32
+    assert rims <= tg.workspace_size(g, "backproject") < rims + (1 << 20)
+    # SIRT-type epilogues keep the owned sums in a volume of their own
+    assert tg.workspace_size(g, "sirt") >= 4 * (2 * nray + 2 * nvox) + rims
 
 
 def test_fdk_weight_options_are_checked_on_the_host(lib):
