@@ -795,14 +795,17 @@ def run_micro(args):
     return 0
 
 
-KERNEL_CASES = ("fp_interp", "fp_siddon", "bp_matched", "bp_fdk", "bp_siddon", "fdk_rows_hamming", "tv_march")
+KERNEL_CASES = ("fp_interp", "fp_siddon", "bp_matched", "bp_fdk", "bp_siddon", "fdk_rows_hamming", "tv_march",
+                "sirt")
 
 
 def run_kernel(args):
     """The capture workload of one kernel for a profiler (no JSON line):
     the half-resolution scan (256^3 at 1 mm, 360 views, 384 x 512 detector:
     inputs above the 129 MB L2, a few GB on the device), one warm-up and one
-    further launch of the named operator; tv_march runs on a 512^3 volume."""
+    further launch of the named operator; tv_march runs on a 512^3 volume;
+    sirt is one SIRT iteration (its backprojections use the split-word
+    accumulation)."""
     import torch
 
     from paper_2412_10129_gb300 import build, inputs, tg
@@ -820,7 +823,9 @@ def run_kernel(args):
            "bp_matched": lambda: tg.backproject(g, b, "matched", out=v),
            "bp_fdk": lambda: tg.backproject(g, b, "fdk", out=v),
            "bp_siddon": lambda: tg.backproject(g, b, "siddon", out=v),
-           "fdk_rows_hamming": lambda: tg.fdk_filter(g, b, "hamming", out=p)}
+           "fdk_rows_hamming": lambda: tg.fdk_filter(g, b, "hamming", out=p),
+           # one SIRT iteration: column weights (split-word BP of ones) and one update
+           "sirt": lambda: tg.sirt(g, b, 1)}
     if args.kernel == "tv_march":
         xt = torch.rand((512, 512, 512), generator=gen, device="cuda")
         fn = lambda: tg.tv_descent(xt, 1, 1e-3)  # noqa: E731
