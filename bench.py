@@ -429,6 +429,10 @@ def run_gpu(args):
         if n:
             roofs[name] = fn(per_step_samples[name] * args.steps, ms * 1e-3, rates)
             roofs[name]["launches_in_timed_region"] = n
+            # DRAM bytes per launch (ncu per-sample figure x this launch's samples)
+            roofs[name]["traffic"] = DRAM_BYTES_PER_SAMPLE[name] * per_step_samples[name] * args.steps / n
+            roofs[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per sample on the "
+                                             "256^3 / 360-view case, scaled by the samples per launch")
     dominant = max(roofs, key=lambda k: kt[k][0])
     roof = dict(roofs[dominant])
     t_fp_live = kt["fp_interp"][0] * 1e-3 / (4 * args.steps)
@@ -478,9 +482,16 @@ def _probe_rates():
             "l2_sector_gather_gbs": probe.sector_gather(64 << 20)["gbs"]}
 
 
-# DRAM bytes (read + write) of one k_bp_matched launch, from an ncu capture of
-# the kernel as built now (profiles/); None until such a capture exists.
-BP_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per interpolated sample, from one ncu capture of
+# each kernel as built now on the 256^3 / 360-view case (3.348e10 samples;
+# profiles/k_fp_interp_tex_medium_256.md, k_bp_mx_medium_256.md,
+# k_bp_mx_split_medium_256.md), scaled to a launch by its samples.  The
+# projector's traffic is the volume and the projections once; the
+# transposes' is dominated by the rays' set-up table, read by every brick a
+# ray passes near, which grows with the samples (rays x bricks per ray).
+DRAM_BYTES_PER_SAMPLE = {"fp_interp": (68.581e6 + 236.597e6) / 3.348e10,
+                         "bp_matched": (20.517e9 + 1.146e9) / 3.348e10,
+                         "bp_matched_split": (20.865e9 + 1.185e9) / 3.348e10}
 
 
 def roofline_bp(samples, t, rates):
@@ -491,7 +502,7 @@ def roofline_bp(samples, t, rates):
     peak = rates["smem_atomic_conflict_free"] / 8.0
     achieved = samples / t
     return {"bound": "smem_atomic", "kernel": "k_bp_mx (fixed point)", "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "Gsamples/s", "frac": achieved / peak, "traffic": BP_TRAFFIC_PER_LAUNCH,
+            "unit": "Gsamples/s", "frac": achieved / peak, "traffic": None,
             "peak_samples_per_s": peak,
             "peak_source": "measured conflict-free shared-memory 32-bit atomic adds (libtgprobe tgp_smem_atomic) / "
                            "8 atomics per sample",
