@@ -26,7 +26,9 @@
 //     faces go to a rim buffer that a merge kernel adds to the neighbours'
 //     sums in a fixed order before the epilogue (scratch: the rim buffer,
 //     and a volume for the modes that read the output).  Lanes take rays
-//     from a per-angle list (long rays first) through a work queue.
+//     from a per-angle list (long rays first, each with its set-up) through
+//     a work queue; the set-ups come from a table that k_ray_table fills once
+//     per launch when it fits in half of the free device memory.
 //   k_bp_matched: bricks grown by a two-voxel rim, every sample of the rim
 //     processed by both bricks (1.27 times the samples), no scratch beyond
 //     one word per batch item: used where the call must not allocate
