@@ -999,12 +999,14 @@ template <class C, int ACC, bool PAR>
 __global__ void __launch_bounds__(C::XT, C::MINB)
     k_bp_mx_ragged(const float *__restrict__ proj, float *__restrict__ sumv, float *__restrict__ rim,
                    const Angle *__restrict__ angles, const __grid_constant__ MxRagged tab,
-                   const unsigned int *__restrict__ absmax) {
+                   const unsigned int *__restrict__ absmax, RayTable tb) {
     const int v = ragged_slot(tab.blk0, tab.nvol, blockIdx.x);
     const int bl = blockIdx.x - tab.blk0[v], nbx = tab.nbx[v], nby = tab.nby[v];
     mx_brick<C, ACC, PAR>(proj + tab.p0[v], sumv + tab.v0[v], rim + tab.r0[v] + (size_t)bl * C::NRIM,
                           angles + tab.a0[v], tab.g[v], __uint_as_float(absmax[v]), bl % nbx, (bl / nbx) % nby,
-                          bl / (nbx * nby), RayTable{nullptr, nullptr, nullptr});
+                          bl / (nbx * nby),
+                          tb.fa ? RayTable{tb.fa + tab.p0[v], tb.fb + tab.p0[v], tb.fc + tab.p0[v]}
+                                : RayTable{nullptr, nullptr, nullptr});
 }
 
 // Owner sum of voxel i of a volume plus the rims of its up to seven lower
@@ -1331,10 +1333,41 @@ cudaError_t launch_mx_ragged(const Grid *gs, const float *scales, int n, const i
     if (in_place) sumv = vol;
     {
         KernelTimer kt(TG_KT_BP_MATCHED, s);
+        // the rays' set-ups of every volume, packed like the projections
+        RayTable tb{nullptr, nullptr, nullptr};
+        void *tbuf = nullptr;
+        {
+            const size_t nray = (size_t)pix, bytes = nray * 36 + 64;
+            size_t fr = 0, tot = 0;
+            if (nray > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes <= fr / 2 &&
+                cudaMallocAsync(&tbuf, bytes, s) == cudaSuccess) {
+                float4 *fa = reinterpret_cast<float4 *>(tbuf), *fb = fa + nray;
+                int *fc = reinterpret_cast<int *>(fb + nray);
+                for (int k = 0; k < n && e == cudaSuccess; ++k) {
+                    const Grid &g = gs[k];
+                    const size_t nk = (size_t)g.nA * g.nv * g.nu;
+                    if (nk == 0) continue;
+                    const size_t nb = (nk + 255) / 256;
+                    const unsigned grid = (unsigned)(nb < 152 * 64 ? nb : 152 * 64);
+                    if (g.parallel)
+                        k_ray_table<true><<<grid, 256, 0, s>>>(d_angles + tab.a0[k], g, fa + tab.p0[k], fb + tab.p0[k],
+                                                               fc + tab.p0[k]);
+                    else
+                        k_ray_table<false><<<grid, 256, 0, s>>>(d_angles + tab.a0[k], g, fa + tab.p0[k], fb + tab.p0[k],
+                                                                fc + tab.p0[k]);
+                    count_launch();
+                    e = cudaGetLastError();
+                }
+                tb = RayTable{fa, fb, fc};
+            } else {
+                cudaGetLastError();
+                tbuf = nullptr;
+            }
+        }
         auto kern = gs[0].parallel ? k_bp_mx_ragged<C, ACC_FIX, true> : k_bp_mx_ragged<C, ACC_FIX, false>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e == cudaSuccess) {
-            kern<<<(unsigned)blocks, C::XT, C::SMEM, s>>>(proj, sumv, rim, d_angles, tab, ep.absmax);
+            kern<<<(unsigned)blocks, C::XT, C::SMEM, s>>>(proj, sumv, rim, d_angles, tab, ep.absmax, tb);
             count_launch();
             e = cudaGetLastError();
         }
@@ -1348,6 +1381,7 @@ cudaError_t launch_mx_ragged(const Grid *gs, const float *scales, int n, const i
             count_launch();
             e = cudaGetLastError();
         }
+        if (tbuf) cudaFreeAsync(tbuf, s);
     }
     cudaFreeAsync(rim, s);
     if (!in_place) cudaFreeAsync(sumv, s);
