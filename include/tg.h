@@ -63,7 +63,7 @@ typedef enum {
     TG_ERR_OOM = 3,         /* scratch allocation failed */
     TG_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed */
     TG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (tg_device_status) */
-    TG_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    TG_ERR_UNSUPPORTED = 6  /* valid request that the library does not implement */
 } tg_status;
 
 /* Forward projector discretisations (the paper names neither; see the
